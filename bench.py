@@ -1,0 +1,447 @@
+"""Benchmark: grid points/s and TFLOP/s of H integration + density on one GB300.
+
+One step = one pass of the whole hot path over the workload: basis
+evaluation, H contraction with sparse FP64 scatter, density contraction and
+the FP64 electron-count traces, for every batch of the grid.  The plan
+(active functions, pattern, work lists) is built once, off the timed path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload si64]
+                    [--precision split_bf16|bf16|fp64] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (weak scaling, no collective on the data
+path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "grid pts/s and TFLOP/s for H-integ+density on 1 GB300, split-BF16 vs FP64 at stated err"
+UNIT = "grid_pts/s"
+KERNEL_SOURCES = {"h": "fgi_tc.cu", "density": "fgi_tc.cu", "basis": "fgi_tc.cu"}
+
+
+def make_workload(name):
+    if name == "tiny":
+        return W.tiny_water(), "tiny water: 3 atoms, 7 fns, 40x110 pts/atom"
+    if name == "si64":
+        return W.si64(), "Si64 cluster: 64 atoms, 1600 fns (6s3p2d), 60x302 pts/atom, batches <=300 pts"
+    if name == "chno1000":
+        return W.chno_cluster(), "1000-atom CHNO cluster, 70x590 pts/atom, uneven batches 50-400 pts"
+    if name.startswith("chno"):
+        n = int(name[4:])
+        return W.chno_cluster(n_atoms=n), "%d-atom CHNO cluster" % n
+    raise SystemExit("unknown workload " + name)
+
+
+def density_matrix(prob, rng):
+    n = prob.n_fn_sys(0)
+    if n <= 4000:
+        D, _ = W.density_matrix_occ(n, max(1, int(round(0.28 * n))), rng)
+        return D
+    return None
+
+
+def stored_values(ctx, M, s=0):
+    rowptr, col = ctx.pattern(s)
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    return M[rows, col], rows, col
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, x in zip(names, f[5:9]):
+                if x.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_gemm_peak(torch):
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(5):
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def traffic_for(kind):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    ent = tab.get(kind)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2208_12335_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def oracle_sample(prob, D, n_batches, seed=7):
+    """The FP64 oracle (H over the active functions + density) on a seeded
+    sample of batches; returns (points, seconds, threads)."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    ids = np.sort(rng.choice(prob.n_batch, size=min(n_batches, prob.n_batch), replace=False))
+    sub = prob.subgrid(ids)
+    B = O.system_basis(sub)
+    act = O.active_functions(B, sub.pts)
+    t0 = time.perf_counter()
+    O.h_matrix(B, sub.pts, sub.w, sub.v, sub=act)
+    if D is not None:
+        O.density(B, sub.pts, D[np.ix_(act, act)], sub=act)
+    else:
+        O.density(B, sub.pts, np.eye(len(act)), sub=act)
+    dt = time.perf_counter() - t0
+    return sub.n_pts, dt, O.num_threads(), len(ids)
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    if rank != 0:
+        return
+    prob, desc = make_workload(args.workload)
+    D = density_matrix(prob, W.rng_for(1, W.PURPOSE_D))
+    nb = args.ref_batches
+    for _ in range(args.warmup):
+        oracle_sample(prob, D, max(1, nb // 4), seed=1)
+    pts_tot, t_tot = 0, 0.0
+    threads = 1
+    for k in range(args.steps):
+        p, dt, threads, _ = oracle_sample(prob, D, nb, seed=100 + k)
+        pts_tot += p
+        t_tot += dt
+    value = pts_tot / t_tot
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": desc, "n_pts": prob.n_pts},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": "%d seeded batches of %d per step (H + density)" % (nb, prob.n_batch)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="si64")
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "bf16", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-batches", type=int, default=12)
+    ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda:%d" % local)
+    from paper_2208_12335_gb300 import Context
+
+    prob, desc = make_workload(args.workload)
+    D = density_matrix(prob, W.rng_for(1, W.PURPOSE_D))
+    t0 = time.perf_counter()
+    ctx = Context(local).load(prob, args.precision)
+    plan_s = time.perf_counter() - t0
+    n_fn, nnz, n_pts, n_at = ctx.sizes()
+    if D is not None:
+        dvals, rows, cols = stored_values(ctx, D)
+    else:
+        rng = W.rng_for(2, W.PURPOSE_D)
+        dvals = rng.standard_normal(nnz) * 0.05
+        rows = cols = None
+    v = torch.from_numpy(prob.v).to(dev)
+    d = torch.from_numpy(dvals).to(dev)
+    h = torch.empty(nnz, dtype=torch.float64, device=dev)
+    n = torch.empty(n_pts, dtype=torch.float64, device=dev)
+    tr = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = ctx.workspace()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.integrate_h(v, h, ws=ws)
+        ctx.density(d, n, tr, ws=ws)
+
+    def timed(nsteps, fn):
+        times = []
+        e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(nsteps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(nsteps):
+            flush.fill_(k & 255)                  # evict L2 between steps (not timed)
+            e[k][0].record(stream)
+            fn()
+            e[k][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        times = [a.elapsed_time(b) for a, b in e]
+        return times
+
+    graph = None
+    if args.graph:
+        s2 = torch.cuda.Stream()
+        with torch.cuda.stream(s2):
+            step()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+
+    run = graph.replay if graph is not None else step
+    for _ in range(args.warmup):
+        run()
+    ctx.sync()
+
+    ctx.profile(True) if graph is None else None
+    with ClockSampler(local) as clk:
+        times = timed(args.steps, run)
+    ms = statistics.mean(times)
+    prof = {}
+    if graph is None:
+        for kind in ("basis", "h", "density", "other"):
+            prof[kind] = ctx.profile_read(kind)
+        ctx.profile(False)
+    ctx.sync()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    # end to end through the public API with host buffers
+    v_h = torch.from_numpy(prob.v).pin_memory()
+    d_h = torch.from_numpy(dvals).pin_memory()
+    h_h = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    n_h = torch.empty(n_pts, dtype=torch.float64).pin_memory()
+    v2 = torch.empty_like(v)
+    d2 = torch.empty_like(d)
+
+    def e2e_step():
+        v2.copy_(v_h, non_blocking=True)
+        d2.copy_(d_h, non_blocking=True)
+        ctx.integrate_h(v2, h, ws=ws)
+        ctx.density(d2, n, tr, ws=ws)
+        h_h.copy_(h, non_blocking=True)
+        n_h.copy_(n, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = timed(max(3, args.steps // 2), e2e_step)
+    e2e_ms = statistics.mean(e2e_times)
+
+    # FP64 GPU path on the same inputs (the comparator)
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        ctx.set_precision("fp64")
+        step()
+        ctx.sync()
+        t64 = timed(args.fp64_steps, step)
+        h64 = h.clone()
+        n64 = n.clone()
+        ctx.set_precision(args.precision)
+        step()
+        ctx.sync()
+        fp64 = {"ms_per_step": statistics.mean(t64),
+                "value": n_pts / (statistics.mean(t64) * 1e-3),
+                "max_abs_dH_vs_fp64_gpu": float((h - h64).abs().max().item()),
+                "density_rel_l2_vs_fp64_gpu": float(((n - n64).norm() / n64.norm()).item())}
+
+    out = None
+    if rank == 0:
+        flops_step = sum(prof[k]["flops"] for k in ("h", "density")) / args.steps if prof else None
+        value = n_pts * world / (ms_max * 1e-3)
+        peaks, peak_src = measured_peaks()
+        # dominant kernel class by measured time
+        roof = None
+        if prof:
+            dom = max(("basis", "h", "density"), key=lambda k: prof[k]["ms"])
+            pk = prof[dom]
+            avg_ms = pk["ms"] / max(1, pk["launches"])
+            per_launch_flops = pk["flops"] / max(1, pk["launches"])
+            per_launch_bytes = pk["bytes"] / max(1, pk["launches"])
+            if dom == "basis":
+                ach = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+                peak = peaks["hbm_gbs"]
+                roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s"}
+            elif args.precision == "fp64":
+                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
+                peak = fp64_gemm_peak(torch)
+                roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "peak_note": "measured FP64 GEMM (cuBLAS) on this GPU"}
+            else:
+                products = 6 if args.precision == "split_bf16" else 1
+                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
+                peak = peaks["bf16_tflops_sustained"] / products
+                roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "peak_note": "%s sustained BF16 / %d BF16 products per algorithmic FLOP"
+                                     % (peak_src, products)}
+            roof["frac"] = roof["achieved"] / roof["peak"]
+            roof["traffic"] = traffic_for(dom)
+            roof["launch_ms"] = avg_ms
+            roof["launches_per_step"] = pk["launches"] / args.steps
+        cpu = None
+        if not args.no_cpu_baseline:
+            p, dt, thr, nbs = oracle_sample(prob, D, args.ref_batches)
+            cpu = {"value": p / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+                   "sample": "%d seeded batches (%d points) of %d, H + density" % (nbs, p, prob.n_batch)}
+        errors = None
+        if not args.no_check and rows is not None:
+            errors = check_against_oracle(prob, ctx, h, n, D, rows, cols)
+        launches = int(sum(prof[k]["launches"] for k in prof) / args.steps) if prof else None
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": {"split_bf16": "split-bf16x3 (f32 acc, f64 cross-batch)", "bf16": "bf16 (f32 acc)",
+                         "fp64": "f64"}[args.precision],
+               "data": "synthetic",
+               "config": {"workload": desc, "n_pts": n_pts, "n_fn": n_fn, "nnz": nnz, "n_atoms": n_at,
+                          "n_batches": prob.n_batch, "precision": args.precision,
+                          "l2": "flushed between steps (256 MiB write)",
+                          "graph": bool(args.graph), "plan_s": round(plan_s, 3)},
+               "tflops": flops_step / (ms_max * 1e-3) / 1e12 if flops_step else None,
+               "roofline": roof,
+               "cpu_baseline": cpu,
+               "e2e": {"value": n_pts * world / (e2e_ms * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
+               "gpu_launches": launches * args.steps if launches is not None else None,
+               "fp64_path": fp64,
+               "errors_vs_oracle": errors,
+               "clocks": clk.summary(),
+               "profile_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof} if prof else None}
+        if fp64:
+            out["speedup_vs_fp64_gpu"] = fp64["ms_per_step"] / ms_max
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def check_against_oracle(prob, ctx, h, n, D, rows, cols, n_pairs=48, n_points=256):
+    """Sampled outputs against the FP64 oracle computed one by one."""
+    import oracle as O
+    rng = np.random.default_rng(2024)
+    B = O.system_basis(prob)
+    hv = h.cpu().numpy()
+    k = rng.choice(len(hv), size=n_pairs, replace=False)
+    ref = O.h_pairs(B, prob.pts, prob.w, prob.v, rows[k], cols[k])
+    pts = rng.choice(prob.n_pts, size=n_points, replace=False)
+    nref = O.density(B, prob.pts[pts], D)
+    nv = n.cpu().numpy()[pts]
+    return {"max_abs_dH_sampled": float(np.max(np.abs(hv[k] - ref))),
+            "max_abs_H_sampled": float(np.max(np.abs(ref))),
+            "density_rel_l2_sampled": float(np.linalg.norm(nv - nref) / np.linalg.norm(nref)),
+            "n_pairs": n_pairs, "n_points": n_points}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * fgi.h -- C ABI of the GB300 library for batched real-space grid
+ * integration with numeric atom-centred orbitals (NAO).
+ *
+ * The paper (FHI-aims, "Development Priorities") names NAO basis sets on
+ * real-space integration grids as the numerical core of the method, and
+ * ("Meeting the Exascale Challenges") GPU offloading of its computational
+ * hotspots, batched matrix-matrix multiplications, sparse matrix operations
+ * and data rearrangement as what large systems need.  This library computes,
+ * for every batch b of grid points and the basis functions that are non-zero
+ * on it,
+ *
+ *   phi_i(r) = u_i(d)/d * Y_lm(d/|d|),   d = r - R_atom(i)              (basis)
+ *   H_ij    += sum_{p in b} w_p v_p phi_i(r_p) phi_j(r_p)  -> sparse H    (integration)
+ *   n(r_p)   = sum_ij phi_i(r_p) D_ij phi_j(r_p)                          (density)
+ *
+ * and the adjoint of L = sum_ij G_ij H_ij.
+ *
+ * Conventions
+ *   - Units: Bohr and Hartree.
+ *   - Every function returns an int status: FGI_OK (0) or a negative error
+ *     code.  fgi_last_error() gives a message owned by the context.  Nothing
+ *     throws across the ABI.
+ *   - Host arrays are read during the call and not retained (the library
+ *     copies what it needs).
+ *   - Device arrays passed to the compute calls are owned by the caller.
+ *     The compute calls allocate nothing: scratch space is a caller-owned
+ *     device buffer of at least fgi_workspace_size() bytes.
+ *   - Compute calls only enqueue work on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*; NULL is the legacy default stream) and
+ *     return; results are ready when the stream is.  Device-side errors
+ *     (bounded waits that ran out, non-finite inputs) are recorded in a
+ *     device status word that fgi_sync() reads.
+ *   - A context serves one CUDA device; calls on one context must not
+ *     overlap in host threads.
+ *
+ * Basis-function numbering: per system, atom by atom; within an atom, the
+ * species' radial shells in order; within a shell of angular momentum l,
+ * m = -l..l (real spherical harmonics without the Condon-Shortley phase).
+ * Systems follow each other: the functions of system s are
+ * fn0(s) .. fn0(s)+n_fn(s)-1.
+ *
+ * Sparse matrices (H, D, adjoint seeds): upper triangle (i <= j) of each
+ * system's matrix in CSR order.  Entry (i, j) is stored when the atoms of i
+ * and j are closer than the sum of their largest cutoffs (a superset of the
+ * pairs whose functions overlap; the others are exactly zero).  Values of
+ * system s occupy [val0(s), val0(s)+nnz(s)) of one array.
+ */
+#ifndef FGI_H
+#define FGI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fgi_ctx fgi_ctx;
+
+enum {
+    FGI_OK = 0,
+    FGI_ERR_ARG = -1,          /* bad argument (NULL, negative size, out of range) */
+    FGI_ERR_STATE = -2,        /* call out of order (e.g. compute before fgi_plan) */
+    FGI_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    FGI_ERR_WORKSPACE = -4,    /* workspace NULL, misaligned or too small */
+    FGI_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out */
+    FGI_ERR_NONFINITE = -6,    /* NaN or Inf met in an input */
+    FGI_ERR_UNSUPPORTED = -7,  /* l > 3, no sm_103 device, ... */
+    FGI_ERR_NOMEM = -8         /* host or plan-time device allocation failed */
+};
+
+typedef enum {
+    FGI_FP64 = 0,        /* every step in FP64 on CUDA cores */
+    FGI_SPLIT_BF16 = 1,  /* contractions as 3-term split BF16 on tcgen05, FP32 accumulate,
+                            FP64 across batches */
+    FGI_BF16 = 2         /* contractions in plain BF16 on tcgen05, FP32 accumulate */
+} fgi_precision;
+
+/* Create a context on CUDA device `cuda_device`.  FGI_ERR_UNSUPPORTED if the
+   device is not compute capability 10.3.  cuda_device = -1 creates a
+   host-only context: inputs, plan tables, pattern and workspace queries
+   work; the compute calls return FGI_ERR_STATE. */
+int fgi_create(fgi_ctx **out, int cuda_device);
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+int fgi_destroy(fgi_ctx *ctx);
+/* Message of the last error on this context ("" if none). */
+const char *fgi_last_error(const fgi_ctx *ctx);
+
+/* Radial function u(r) (= r R(r)) as a uniform cubic spline on r_k = k h,
+   k = 0..n_knots-1, with cutoff r_cut = (n_knots-1) h and u = 0 beyond it.
+   coef: host [n_knots-1][4] doubles; on [r_k, r_k+1],
+   u(r) = c0 + t (c1 + t (c2 + t c3)), t = (r - r_k)/h.  0 <= l <= 3.
+   The basis function is phi = u(d)/d * Y_lm (the paper's NAO basis,
+   "Development Priorities"). */
+int fgi_add_radial(fgi_ctx *ctx, int l, double h, int n_knots, const double *coef,
+                   int *radial_id_out);
+
+/* Species with nuclear charge Z and n_shell radial shells (radial ids from
+   fgi_add_radial); each shell of angular momentum l gives 2l+1 functions. */
+int fgi_add_species(fgi_ctx *ctx, double Z, int n_shell, const int *radial_id,
+                    int *species_id_out);
+
+/* n_sys independent systems (the paper's ensemble runs, "Concluding
+   Remarks"); atom_off[n_sys+1] (host, int64) splits the atom arrays;
+   species[n_atoms] (host); xyz[n_atoms][3] (host, Bohr).  Replaces any
+   previous systems and invalidates the plan. */
+int fgi_set_systems(fgi_ctx *ctx, int n_sys, const int64_t *atom_off, const int *species,
+                    const double *xyz);
+
+/* Integration grid: n_pts points xyz[n_pts][3] and weights w[n_pts] (host),
+   grouped into n_batch batches of consecutive points, batch b being
+   [batch_off[b], batch_off[b+1]) and belonging to system batch_sys[b].
+   A batch may hold at most 1024 points.  Invalidates the plan. */
+int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w,
+                 int64_t n_batch, const int64_t *batch_off, const int *batch_sys);
+
+/* Build the plan (host, once per geometry and grid): the functions active
+   on each batch, the sparsity pattern of H, the tile work lists, and the
+   device copies of the inputs.  tune_cache_path: NULL for default tiles, or
+   a file of tuned settings written by the autotuner. */
+int fgi_plan(fgi_ctx *ctx, fgi_precision precision, const char *tune_cache_path);
+
+/* Change the precision of later compute calls without re-planning. */
+int fgi_set_precision(fgi_ctx *ctx, fgi_precision precision);
+
+/* Sizes after fgi_plan: total functions, total stored values (all
+   systems), total points and atoms. */
+int fgi_get_sizes(fgi_ctx *ctx, int64_t *n_fn, int64_t *nnz, int64_t *n_pts, int64_t *n_atoms);
+
+/* Per-system layout: first function, function count, first value, value count. */
+int fgi_get_system(fgi_ctx *ctx, int sys, int64_t *fn0, int64_t *n_fn, int64_t *val0,
+                   int64_t *nnz);
+
+/* CSR pattern of system `sys` (host arrays owned by the context, valid until
+   the next fgi_plan/fgi_set_*): rowptr[n_fn(sys)+1] (relative to val0(sys))
+   and col[nnz(sys)] (function index within the system). */
+int fgi_get_pattern(fgi_ctx *ctx, int sys, int64_t *nnz, const int64_t **rowptr,
+                    const int **col);
+
+/* Bytes of device scratch space the compute calls need (for every
+   precision). */
+int fgi_workspace_size(fgi_ctx *ctx, size_t *bytes);
+
+/* H integration: h[val] (+)= sum_b sum_{p in b} w_p v_p phi_i phi_j for every
+   stored (i, j).  v_dev: device [n_pts] FP64; h_dev: device [nnz] FP64,
+   overwritten (accumulate = 0) or added to (accumulate = 1).  Cross-batch
+   accumulation is FP64 in every precision. */
+int fgi_integrate_h(fgi_ctx *ctx, const double *v_dev, double *h_dev, int accumulate,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Density: n_dev[p] = sum_ij phi_i(r_p) D_ij phi_j(r_p), in the caller's
+   point order, D the symmetric matrix whose upper triangle d_dev[nnz]
+   (device FP64) stores.  traces_dev (device [n_sys] FP64, may be NULL)
+   receives N_el(s) = sum_{p in s} w_p n_p. */
+int fgi_density(fgi_ctx *ctx, const double *d_dev, double *n_dev, double *traces_dev,
+                void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of L = sum_stored g_k h_k (g_dev: device [nnz], the gradient of L
+   with respect to the stored values of H): with G the symmetric matrix
+   G_ii = g_ii, G_ij = G_ji = g_ij/2, and the grid held fixed while atoms move,
+     dv_dev[p]   = w_p sum_ij G_ij phi_i phi_j                      [n_pts]
+     dR_dev[a,:] = -2 sum_p w_p v_p sum_{i on a} grad phi_i . (G phi)_i  [n_atoms][3]
+   v_dev is the potential of the forward call.  All device FP64. */
+int fgi_adjoint(fgi_ctx *ctx, const double *g_dev, const double *v_dev, double *dv_dev,
+                double *dR_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* out_dev[s] = sum_ij A_ij B_ij over system s's full symmetric matrices
+   stored as upper triangles a_dev, b_dev (device [nnz] FP64): tr(DS) with
+   A = D, B = S, or the band energy with B = H.  FP64. */
+int fgi_trace(fgi_ctx *ctx, const double *a_dev, const double *b_dev, double *out_dev,
+              void *stream);
+
+/* Wait for the stream and read the device status word: FGI_OK,
+   FGI_ERR_TIMEOUT or FGI_ERR_NONFINITE (the word is cleared after reading). */
+int fgi_sync(fgi_ctx *ctx, void *stream);
+
+/* Kernel classes for the launch profile. */
+enum {
+    FGI_KERNEL_BASIS = 0,     /* basis evaluation (and operand images) */
+    FGI_KERNEL_H = 1,         /* H contraction + sparse scatter */
+    FGI_KERNEL_DENSITY = 2,   /* density contraction */
+    FGI_KERNEL_ADJOINT = 3,   /* adjoint position gradient */
+    FGI_KERNEL_OTHER = 4      /* reductions and traces */
+};
+
+/* Launch profile: enable = 1 clears the record and starts timing every
+   launch of the library's kernels with CUDA events on the call's stream;
+   enable = 0 stops.  Not for use inside stream capture. */
+int fgi_profile(fgi_ctx *ctx, int enable);
+
+/* Totals over the recorded launches of one kernel class: number of
+   launches, summed event time (ms), and the algorithmic FLOPs and bytes
+   those launches had to process (per batch: H 2 P n^2, density
+   2 P n^2 + 2 P n, scatter 16 bytes per stored upper entry, with P points
+   and n active functions).  Waits for the recorded events. */
+int fgi_profile_read(fgi_ctx *ctx, int kind, int64_t *launches, double *ms, double *flops,
+                     double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGI_H */

@@ -1,0 +1,965 @@
+// Host runtime of the C ABI: input tables, the plan (active functions per
+// batch, sparsity pattern, tile work lists, waves), device storage, and the
+// call sequences of the compute entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fgi_internal.h"
+#include "fgi_tc.h"
+#include "../../include/fgi.h"
+
+using namespace fgi;
+
+namespace {
+
+struct RadialH {
+    int l;
+    double h;
+    int nk;
+    std::vector<double> coef;
+};
+
+struct SpeciesH {
+    double Z;
+    std::vector<int> shells;
+    int n_fn;
+    double rcut;
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+
+struct Wave {
+    double phi_flops = 0, phi_bytes = 0, h_flops = 0, h_bytes = 0, n_flops = 0, n_bytes = 0;
+    int b0 = 0, nb = 0;            // batch range
+    long long it0 = 0, nit = 0;    // items range (H tiles, FP64)
+    long long dt0 = 0, ndt = 0;    // items range (density tiles, FP64)
+    size_t ws_elems = 0;           // FP64 elements of the Phi block
+};
+
+template <typename T>
+struct Slot {                     // an array inside the device arena
+    size_t off = 0, n = 0;
+};
+
+}  // namespace
+
+struct fgi_ctx {
+    int device = 0;
+    std::string err;
+    std::vector<RadialH> radials;
+    std::vector<SpeciesH> species;
+    // systems
+    int n_sys = 0;
+    std::vector<int64_t> atom_off;
+    std::vector<int> atom_species;
+    std::vector<double> atom_xyz;
+    bool have_systems = false;
+    // grid
+    int64_t n_pts = 0;
+    std::vector<double> pts, w;
+    std::vector<int64_t> batch_off;
+    std::vector<int> batch_sys;
+    bool have_grid = false;
+    // plan
+    bool planned = false;
+    fgi_precision precision = FGI_FP64;
+    int64_t n_fn = 0, nnz = 0;
+    std::vector<long long> atom_fn0;
+    std::vector<int> atom_loc, atom_nfn, atom_sys;
+    std::vector<int64_t> sys_fn0, sys_nfn, sys_val0, sys_nnz;
+    std::vector<long long> rowptr;            // global value index per global function
+    std::vector<int> fn_sys;
+    std::vector<int> pairpos;
+    std::vector<long long> sys_pair_off;
+    std::vector<std::vector<int>> nbr;        // per atom: neighbour atoms b >= a (global)
+    std::vector<DevBatch> batches_f64;
+    std::vector<DevAct> act;
+    std::vector<Wave> waves;
+    std::vector<WorkItem> items;
+    size_t ws_f64_bytes = 0;
+    // pattern cache for fgi_get_pattern
+    int pattern_sys = -1;
+    std::vector<int64_t> pat_rowptr;
+    std::vector<int> pat_col;
+    // device
+    char *d_arena = nullptr;
+    size_t arena_bytes = 0;
+    DevPlan dp{};
+    DevBatch *d_batches_f64 = nullptr;
+    WorkItem *d_items = nullptr;
+    long long *d_sys_val0 = nullptr, *d_sys_fn0 = nullptr;
+    int *d_fn_sys = nullptr;
+    int *d_status = nullptr;
+    TcPlan tc;                                // tensor-core path plan
+    // per-kernel CUDA-event profile
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRec> recs;
+    long long prof_dropped = 0;
+};
+
+namespace {
+
+int set_err(fgi_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define CUDA_TRY(c, expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_err(c, FGI_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));       \
+    } while (0)
+
+void free_device(fgi_ctx *c)
+{
+    if (c->d_arena) cudaFree(c->d_arena);
+    c->d_arena = nullptr;
+    c->arena_bytes = 0;
+    tc_free(c->tc);
+    c->planned = false;
+}
+
+void invalidate(fgi_ctx *c)
+{
+    c->planned = false;
+    c->pattern_sys = -1;
+    c->pat_rowptr.clear();
+    c->pat_col.clear();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void wave_work(fgi_ctx *c);
+
+// ------------------------------------------------------------ plan building
+int build_plan(fgi_ctx *c, const char *tune_path)
+{
+    const int n_at = (int)c->atom_species.size();
+    // atoms
+    c->atom_fn0.assign(n_at, 0);
+    c->atom_loc.assign(n_at, 0);
+    c->atom_nfn.assign(n_at, 0);
+    c->atom_sys.assign(n_at, 0);
+    c->sys_fn0.assign(c->n_sys, 0);
+    c->sys_nfn.assign(c->n_sys, 0);
+    long long fn = 0;
+    for (int s = 0; s < c->n_sys; s++) {
+        c->sys_fn0[s] = fn;
+        for (int64_t a = c->atom_off[s]; a < c->atom_off[s + 1]; a++) {
+            c->atom_fn0[a] = fn;
+            c->atom_loc[a] = (int)(a - c->atom_off[s]);
+            c->atom_nfn[a] = c->species[c->atom_species[a]].n_fn;
+            c->atom_sys[a] = s;
+            fn += c->atom_nfn[a];
+        }
+        c->sys_nfn[s] = fn - c->sys_fn0[s];
+    }
+    c->n_fn = fn;
+    // pattern: neighbour lists, row pointers, pair positions
+    c->nbr.assign(n_at, {});
+    c->rowptr.assign(c->n_fn, 0);
+    c->fn_sys.assign(c->n_fn, 0);
+    c->sys_val0.assign(c->n_sys, 0);
+    c->sys_nnz.assign(c->n_sys, 0);
+    c->sys_pair_off.assign(c->n_sys, 0);
+    long long pair_total = 0;
+    for (int s = 0; s < c->n_sys; s++) {
+        long long nat = c->atom_off[s + 1] - c->atom_off[s];
+        c->sys_pair_off[s] = pair_total;
+        pair_total += nat * nat;
+    }
+    c->pairpos.assign(pair_total, -1);
+    long long cursor = 0;
+    for (int s = 0; s < c->n_sys; s++) {
+        c->sys_val0[s] = cursor;
+        const int64_t a0 = c->atom_off[s], a1 = c->atom_off[s + 1];
+        const long long nat = a1 - a0;
+        for (int64_t a = a0; a < a1; a++) {
+            const double ra = c->species[c->atom_species[a]].rcut;
+            const double *xa = &c->atom_xyz[3 * a];
+            long long pos = 0;
+            for (int64_t b = a; b < a1; b++) {
+                const double rb = c->species[c->atom_species[b]].rcut;
+                const double *xb = &c->atom_xyz[3 * b];
+                const double dx = xa[0] - xb[0], dy = xa[1] - xb[1], dz = xa[2] - xb[2];
+                if (b == a || std::sqrt(dx * dx + dy * dy + dz * dz) < ra + rb) {
+                    c->nbr[a].push_back((int)b);
+                    c->pairpos[c->sys_pair_off[s] + (a - a0) * nat + (b - a0)] = (int)pos;
+                    pos += c->atom_nfn[b];
+                }
+            }
+            const long long RL = pos;
+            for (int li = 0; li < c->atom_nfn[a]; li++) {
+                c->rowptr[c->atom_fn0[a] + li] = cursor;
+                c->fn_sys[c->atom_fn0[a] + li] = s;
+                cursor += RL - li;
+            }
+        }
+        c->sys_nnz[s] = cursor - c->sys_val0[s];
+    }
+    c->nnz = cursor;
+    if (c->nnz > (long long)1 << 40) return set_err(c, FGI_ERR_UNSUPPORTED, "pattern too large");
+
+    // active atoms per batch
+    const int64_t nb = (int64_t)c->batch_sys.size();
+    std::vector<std::vector<int>> active(nb);
+    bool too_many = false;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nb; b++) {
+        const int64_t p0 = c->batch_off[b], p1 = c->batch_off[b + 1];
+        const int s = c->batch_sys[b];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t p = p0; p < p1; p++)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = std::min(lo[k], c->pts[3 * p + k]);
+                hi[k] = std::max(hi[k], c->pts[3 * p + k]);
+            }
+        double cen[3], rad2 = 0.0;
+        for (int k = 0; k < 3; k++) cen[k] = 0.5 * (lo[k] + hi[k]);
+        for (int64_t p = p0; p < p1; p++) {
+            double d2 = 0.0;
+            for (int k = 0; k < 3; k++) d2 += (c->pts[3 * p + k] - cen[k]) * (c->pts[3 * p + k] - cen[k]);
+            rad2 = std::max(rad2, d2);
+        }
+        const double rad = std::sqrt(rad2);
+        int nfn_b = 0;
+        for (int64_t a = c->atom_off[s]; a < c->atom_off[s + 1]; a++) {
+            const double rc = c->species[c->atom_species[a]].rcut;
+            const double *xa = &c->atom_xyz[3 * a];
+            double dc = 0.0;
+            for (int k = 0; k < 3; k++) dc += (xa[k] - cen[k]) * (xa[k] - cen[k]);
+            dc = std::sqrt(dc);
+            if (dc >= rad + rc) continue;
+            bool on = dc + rad < rc;
+            for (int64_t p = p0; p < p1 && !on; p++) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; k++) d2 += (c->pts[3 * p + k] - xa[k]) * (c->pts[3 * p + k] - xa[k]);
+                on = d2 < rc * rc;
+            }
+            if (on) {
+                active[b].push_back((int)a);
+                nfn_b += c->atom_nfn[a];
+            }
+        }
+        if (nfn_b > kMaxBatchFns) too_many = true;
+    }
+    if (too_many)
+        return set_err(c, FGI_ERR_UNSUPPORTED, "a batch has more than %d active functions; use smaller batches",
+                       kMaxBatchFns);
+
+    // batches, active entries, FP64 waves and work items
+    c->act.clear();
+    c->batches_f64.assign(nb, DevBatch{});
+    for (int64_t b = 0; b < nb; b++) {
+        DevBatch &B = c->batches_f64[b];
+        B.pt0 = c->batch_off[b];
+        B.np = (int)(c->batch_off[b + 1] - c->batch_off[b]);
+        B.sys = c->batch_sys[b];
+        B.act0 = (int)c->act.size();
+        B.n_act = (int)active[b].size();
+        int fl = 0;
+        for (int a : active[b]) {
+            c->act.push_back(DevAct{a, fl});
+            fl += c->atom_nfn[a];
+        }
+        B.nfn = fl;
+        B.kpad = (B.np + 31) / 32 * 32;
+    }
+    const size_t wave_cap = (size_t)1 << 27;   // FP64 elements (1 GiB) of Phi per wave
+    c->waves.clear();
+    c->items.clear();
+    {
+        Wave wv;
+        size_t off = 0;
+        for (int64_t b = 0; b < nb; b++) {
+            DevBatch &B = c->batches_f64[b];
+            const size_t need = (size_t)B.nfn * B.kpad;
+            if (wv.nb > 0 && off + need > wave_cap) {
+                wv.ws_elems = off;
+                c->waves.push_back(wv);
+                wv = Wave{};
+                wv.b0 = (int)b;
+                off = 0;
+            }
+            if (wv.nb == 0) wv.b0 = (int)b;
+            B.ws_off = (long long)off;
+            off += align_up(need, 32);
+            wv.nb++;
+        }
+        if (wv.nb > 0) {
+            wv.ws_elems = off;
+            c->waves.push_back(wv);
+        }
+        size_t max_elems = 0;
+        for (Wave &w : c->waves) {
+            w.it0 = (long long)c->items.size();
+            for (int b = w.b0; b < w.b0 + w.nb; b++) {
+                const int nt = (c->batches_f64[b].nfn + 63) / 64;
+                for (int i = 0; i < nt; i++)
+                    for (int j = i; j < nt; j++) c->items.push_back(WorkItem{b, (short)i, (short)j});
+            }
+            w.nit = (long long)c->items.size() - w.it0;
+            w.dt0 = (long long)c->items.size();
+            for (int b = w.b0; b < w.b0 + w.nb; b++) {
+                if (c->batches_f64[b].nfn == 0) continue;
+                const int nt = (c->batches_f64[b].np + 63) / 64;
+                for (int i = 0; i < nt; i++) c->items.push_back(WorkItem{b, (short)i, 0});
+            }
+            w.ndt = (long long)c->items.size() - w.dt0;
+            max_elems = std::max(max_elems, w.ws_elems);
+        }
+        c->ws_f64_bytes = 2 * max_elems * sizeof(double) + 256;   // Phi + E (adjoint)
+    }
+    wave_work(c);
+
+    // ---- device arena
+    free_device(c);
+    if (c->device < 0) {
+        TcPlanInput tin;
+        tin.n_batch = (int)nb;
+        tin.batches = c->batches_f64.data();
+        tin.act = c->act.data();
+        tin.atom_nfn = c->atom_nfn.data();
+        tin.tune_path = tune_path;
+        tin.host_only = true;
+        std::string terr;
+        int rc = tc_build(c->tc, tin, &terr);
+        if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
+        c->planned = true;
+        return FGI_OK;
+    }
+    std::vector<DevRadial> drad;
+    std::vector<double> coef;
+    for (const RadialH &r : c->radials) {
+        DevRadial d;
+        d.h = r.h;
+        d.inv_h = 1.0 / r.h;
+        d.rcut = r.h * (r.nk - 1);
+        d.coef_off = (long long)(coef.size() / 4);
+        d.nk = r.nk;
+        d.l = r.l;
+        coef.insert(coef.end(), r.coef.begin(), r.coef.end());
+        drad.push_back(d);
+    }
+    std::vector<float> coef32(coef.begin(), coef.end());
+    std::vector<DevSpecies> dsp;
+    std::vector<int> shell_rad;
+    for (const SpeciesH &s : c->species) {
+        DevSpecies d;
+        d.shell0 = (int)shell_rad.size();
+        d.n_shell = (int)s.shells.size();
+        d.n_fn = s.n_fn;
+        d.pad = 0;
+        d.rcut = s.rcut;
+        shell_rad.insert(shell_rad.end(), s.shells.begin(), s.shells.end());
+        dsp.push_back(d);
+    }
+    std::vector<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
+    for (int64_t p = 0; p < c->n_pts; p++) {
+        px[p] = c->pts[3 * p];
+        py[p] = c->pts[3 * p + 1];
+        pz[p] = c->pts[3 * p + 2];
+    }
+    std::vector<int> sys_nat(c->n_sys);
+    for (int s = 0; s < c->n_sys; s++) sys_nat[s] = (int)(c->atom_off[s + 1] - c->atom_off[s]);
+    std::vector<long long> sys_val0(c->sys_val0.begin(), c->sys_val0.end());
+    std::vector<long long> sys_fn0(c->sys_fn0.begin(), c->sys_fn0.end());
+
+    struct Blob {
+        const void *src;
+        size_t bytes;
+        size_t off;
+    };
+    std::vector<Blob> blobs;
+    size_t total = 0;
+    auto add = [&](const void *src, size_t bytes) {
+        Blob b{src, bytes, total};
+        total = align_up(total + std::max<size_t>(bytes, 1), 256);
+        blobs.push_back(b);
+        return blobs.size() - 1;
+    };
+    size_t i_px = add(px.data(), px.size() * 8), i_py = add(py.data(), py.size() * 8),
+           i_pz = add(pz.data(), pz.size() * 8), i_pw = add(c->w.data(), c->w.size() * 8),
+           i_axyz = add(c->atom_xyz.data(), c->atom_xyz.size() * 8),
+           i_asp = add(c->atom_species.data(), c->atom_species.size() * 4),
+           i_afn0 = add(c->atom_fn0.data(), c->atom_fn0.size() * 8),
+           i_aloc = add(c->atom_loc.data(), c->atom_loc.size() * 4),
+           i_sp = add(dsp.data(), dsp.size() * sizeof(DevSpecies)),
+           i_shr = add(shell_rad.data(), shell_rad.size() * 4),
+           i_rad = add(drad.data(), drad.size() * sizeof(DevRadial)),
+           i_coef = add(coef.data(), coef.size() * 8), i_coef32 = add(coef32.data(), coef32.size() * 4),
+           i_snat = add(sys_nat.data(), sys_nat.size() * 4),
+           i_spo = add(c->sys_pair_off.data(), c->sys_pair_off.size() * 8),
+           i_pp = add(c->pairpos.data(), c->pairpos.size() * 4),
+           i_rp = add(c->rowptr.data(), c->rowptr.size() * 8),
+           i_bf = add(c->batches_f64.data(), c->batches_f64.size() * sizeof(DevBatch)),
+           i_act = add(c->act.data(), c->act.size() * sizeof(DevAct)),
+           i_items = add(c->items.data(), c->items.size() * sizeof(WorkItem)),
+           i_sv0 = add(sys_val0.data(), sys_val0.size() * 8), i_sf0 = add(sys_fn0.data(), sys_fn0.size() * 8),
+           i_fsys = add(c->fn_sys.data(), c->fn_sys.size() * 4), i_status = add(nullptr, 64);
+    cudaError_t e = cudaMalloc((void **)&c->d_arena, total);
+    if (e != cudaSuccess) {
+        c->d_arena = nullptr;
+        return set_err(c, FGI_ERR_NOMEM, "plan: cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
+    }
+    c->arena_bytes = total;
+    for (const Blob &b : blobs) {
+        if (b.src && b.bytes) CUDA_TRY(c, cudaMemcpy(c->d_arena + b.off, b.src, b.bytes, cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(c, cudaMemset(c->d_arena + blobs[i_status].off, 0, 64));
+    auto at = [&](size_t i) { return (void *)(c->d_arena + blobs[i].off); };
+    DevPlan &P = c->dp;
+    P.px = (const double *)at(i_px);
+    P.py = (const double *)at(i_py);
+    P.pz = (const double *)at(i_pz);
+    P.pw = (const double *)at(i_pw);
+    P.atom_xyz = (const double *)at(i_axyz);
+    P.atom_species = (const int *)at(i_asp);
+    P.atom_fn0 = (const long long *)at(i_afn0);
+    P.atom_loc = (const int *)at(i_aloc);
+    P.species = (const DevSpecies *)at(i_sp);
+    P.shell_rad = (const int *)at(i_shr);
+    P.radials = (const DevRadial *)at(i_rad);
+    P.coef = (const double *)at(i_coef);
+    P.coef32 = (const float *)at(i_coef32);
+    P.sys_nat = (const int *)at(i_snat);
+    P.sys_pair_off = (const long long *)at(i_spo);
+    P.pairpos = (const int *)at(i_pp);
+    P.rowptr = (const long long *)at(i_rp);
+    P.batches = (const DevBatch *)at(i_bf);
+    P.act = (const DevAct *)at(i_act);
+    P.status = (int *)at(i_status);
+    c->d_batches_f64 = (DevBatch *)at(i_bf);
+    c->d_items = (WorkItem *)at(i_items);
+    c->d_sys_val0 = (long long *)at(i_sv0);
+    c->d_sys_fn0 = (long long *)at(i_sf0);
+    c->d_fn_sys = (int *)at(i_fsys);
+    c->d_status = (int *)at(i_status);
+
+    // tensor-core path plan (operand images, tiles, waves)
+    TcPlanInput tin;
+    tin.n_batch = (int)nb;
+    tin.batches = c->batches_f64.data();
+    tin.act = c->act.data();
+    tin.atom_nfn = c->atom_nfn.data();
+    tin.tune_path = tune_path;
+    std::string terr;
+    int rc = tc_build(c->tc, tin, &terr);
+    if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
+    c->planned = true;
+    return FGI_OK;
+}
+
+int check_ready(fgi_ctx *c)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (!c->planned) return set_err(c, FGI_ERR_STATE, "call fgi_plan first");
+    return FGI_OK;
+}
+
+int check_compute(fgi_ctx *c)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->device < 0) return set_err(c, FGI_ERR_STATE, "host-only context (device -1) cannot compute");
+    return FGI_OK;
+}
+
+size_t workspace_need(fgi_ctx *c) { return std::max(c->ws_f64_bytes, tc_workspace_bytes(c->tc)); }
+
+int check_ws(fgi_ctx *c, void *ws, size_t bytes)
+{
+    if (!ws || ((uintptr_t)ws & 255)) return set_err(c, FGI_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+    if (bytes < workspace_need(c))
+        return set_err(c, FGI_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", bytes, workspace_need(c));
+    return FGI_OK;
+}
+
+// Launch-profiling scope: events around one launch on the call's stream.
+struct ProfScope {
+    fgi_ctx *c;
+    cudaStream_t s;
+    int kind;
+    double flops, bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(fgi_ctx *c_, cudaStream_t s_, int kind_, double f, double by)
+        : c(c_), s(s_), kind(kind_), flops(f), bytes(by)
+    {
+        if (!c->prof_on) return;
+        if (c->ev_used + 2 > c->ev_pool.size()) {
+            c->prof_dropped++;
+            return;
+        }
+        a = c->ev_pool[c->ev_used++];
+        b = c->ev_pool[c->ev_used++];
+        cudaEventRecord(a, s);
+    }
+    ~ProfScope()
+    {
+        if (!a) return;
+        cudaEventRecord(b, s);
+        c->recs.push_back(ProfRec{kind, a, b, flops, bytes});
+    }
+};
+
+void wave_work(fgi_ctx *c)
+{
+    for (Wave &w : c->waves) {
+        for (int b = w.b0; b < w.b0 + w.nb; b++) {
+            const DevBatch &B = c->batches_f64[b];
+            const double P = B.np, n = B.nfn;
+            w.phi_flops += 30.0 * P * n;
+            w.phi_bytes += 32.0 * P + 8.0 * P * n;
+            w.h_flops += P * n * (n + 1.0);          // upper triangle incl. diagonal
+            w.h_bytes += 16.0 * n * (n + 1) / 2 + 16.0 * P;
+            w.n_flops += 2.0 * P * n * n + 2.0 * P * n;
+            w.n_bytes += 8.0 * n * n + 16.0 * P;
+        }
+    }
+}
+
+}  // namespace
+
+// ================================================================== the ABI
+extern "C" {
+
+int fgi_create(fgi_ctx **out, int cuda_device)
+{
+    if (!out) return FGI_ERR_ARG;
+    *out = nullptr;
+    if (cuda_device == -1) {            // host-only context: inputs and plan tables, no compute
+        fgi_ctx *c = new (std::nothrow) fgi_ctx();
+        if (!c) return FGI_ERR_NOMEM;
+        c->device = -1;
+        *out = c;
+        return FGI_OK;
+    }
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n)
+        return FGI_ERR_ARG;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) return FGI_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return FGI_ERR_UNSUPPORTED;
+    fgi_ctx *c = new (std::nothrow) fgi_ctx();
+    if (!c) return FGI_ERR_NOMEM;
+    c->device = cuda_device;
+    *out = c;
+    return FGI_OK;
+}
+
+int fgi_destroy(fgi_ctx *c)
+{
+    if (!c) return FGI_OK;
+    if (c->device >= 0) {
+        DeviceGuard g(c->device);
+        free_device(c);
+        for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    }
+    delete c;
+    return FGI_OK;
+}
+
+const char *fgi_last_error(const fgi_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int fgi_add_radial(fgi_ctx *c, int l, double h, int n_knots, const double *coef, int *id_out)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (l < 0 || l > kMaxL) return set_err(c, FGI_ERR_UNSUPPORTED, "l = %d; 0 <= l <= %d supported", l, kMaxL);
+    if (!(h > 0.0) || !std::isfinite(h) || n_knots < 2 || !coef)
+        return set_err(c, FGI_ERR_ARG, "radial: need h > 0, n_knots >= 2, coef");
+    RadialH r;
+    r.l = l;
+    r.h = h;
+    r.nk = n_knots;
+    r.coef.assign(coef, coef + 4 * (size_t)(n_knots - 1));
+    for (double x : r.coef)
+        if (!std::isfinite(x)) return set_err(c, FGI_ERR_NONFINITE, "radial coefficients not finite");
+    c->radials.push_back(std::move(r));
+    if (id_out) *id_out = (int)c->radials.size() - 1;
+    invalidate(c);
+    return FGI_OK;
+}
+
+int fgi_add_species(fgi_ctx *c, double Z, int n_shell, const int *radial_id, int *id_out)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (n_shell < 1 || !radial_id) return set_err(c, FGI_ERR_ARG, "species: need n_shell >= 1");
+    SpeciesH s;
+    s.Z = Z;
+    s.n_fn = 0;
+    s.rcut = 0.0;
+    for (int k = 0; k < n_shell; k++) {
+        int r = radial_id[k];
+        if (r < 0 || r >= (int)c->radials.size()) return set_err(c, FGI_ERR_ARG, "species: bad radial id %d", r);
+        s.shells.push_back(r);
+        s.n_fn += 2 * c->radials[r].l + 1;
+        s.rcut = std::max(s.rcut, c->radials[r].h * (c->radials[r].nk - 1));
+    }
+    c->species.push_back(std::move(s));
+    if (id_out) *id_out = (int)c->species.size() - 1;
+    invalidate(c);
+    return FGI_OK;
+}
+
+int fgi_set_systems(fgi_ctx *c, int n_sys, const int64_t *atom_off, const int *species,
+                    const double *xyz)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (n_sys < 1 || !atom_off || atom_off[0] != 0) return set_err(c, FGI_ERR_ARG, "systems: bad atom_off");
+    for (int s = 0; s < n_sys; s++)
+        if (atom_off[s + 1] < atom_off[s]) return set_err(c, FGI_ERR_ARG, "systems: atom_off not ascending");
+    const int64_t na = atom_off[n_sys];
+    if (na > 0 && (!species || !xyz)) return set_err(c, FGI_ERR_ARG, "systems: NULL arrays");
+    for (int64_t a = 0; a < na; a++) {
+        if (species[a] < 0 || species[a] >= (int)c->species.size())
+            return set_err(c, FGI_ERR_ARG, "systems: bad species id at atom %lld", (long long)a);
+        for (int k = 0; k < 3; k++)
+            if (!std::isfinite(xyz[3 * a + k])) return set_err(c, FGI_ERR_NONFINITE, "systems: xyz not finite");
+    }
+    c->n_sys = n_sys;
+    c->atom_off.assign(atom_off, atom_off + n_sys + 1);
+    c->atom_species.assign(species, species + na);
+    c->atom_xyz.assign(xyz, xyz + 3 * na);
+    c->have_systems = true;
+    invalidate(c);
+    return FGI_OK;
+}
+
+int fgi_set_grid(fgi_ctx *c, int64_t n_pts, const double *xyz, const double *w, int64_t n_batch,
+                 const int64_t *batch_off, const int *batch_sys)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (n_pts < 0 || n_batch < 0 || (n_pts > 0 && (!xyz || !w)) || !batch_off || (n_batch > 0 && !batch_sys))
+        return set_err(c, FGI_ERR_ARG, "grid: bad arguments");
+    if (batch_off[0] != 0 || batch_off[n_batch] != n_pts) return set_err(c, FGI_ERR_ARG, "grid: batch_off must span [0, n_pts]");
+    for (int64_t b = 0; b < n_batch; b++) {
+        const int64_t np = batch_off[b + 1] - batch_off[b];
+        if (np < 0 || np > kMaxBatchPoints)
+            return set_err(c, FGI_ERR_ARG, "grid: batch %lld has %lld points (0..%d allowed)", (long long)b,
+                           (long long)np, kMaxBatchPoints);
+        if (batch_sys[b] < 0) return set_err(c, FGI_ERR_ARG, "grid: bad batch_sys");
+    }
+    for (int64_t p = 0; p < n_pts; p++)
+        if (!std::isfinite(w[p]) || !std::isfinite(xyz[3 * p]) || !std::isfinite(xyz[3 * p + 1]) ||
+            !std::isfinite(xyz[3 * p + 2]))
+            return set_err(c, FGI_ERR_NONFINITE, "grid: point %lld not finite", (long long)p);
+    c->n_pts = n_pts;
+    c->pts.assign(xyz, xyz + 3 * n_pts);
+    c->w.assign(w, w + n_pts);
+    c->batch_off.assign(batch_off, batch_off + n_batch + 1);
+    c->batch_sys.assign(batch_sys, batch_sys + n_batch);
+    c->have_grid = true;
+    invalidate(c);
+    return FGI_OK;
+}
+
+int fgi_plan(fgi_ctx *c, fgi_precision precision, const char *tune_cache_path)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (!c->have_systems || !c->have_grid) return set_err(c, FGI_ERR_STATE, "set systems and grid before fgi_plan");
+    if (precision != FGI_FP64 && precision != FGI_SPLIT_BF16 && precision != FGI_BF16)
+        return set_err(c, FGI_ERR_ARG, "unknown precision %d", (int)precision);
+    for (int b : c->batch_sys)
+        if (b >= c->n_sys) return set_err(c, FGI_ERR_ARG, "grid: batch_sys out of range");
+    invalidate(c);
+    if (c->device < 0) {
+        c->precision = precision;
+        try {
+            return build_plan(c, tune_cache_path);
+        } catch (const std::bad_alloc &) {
+            return set_err(c, FGI_ERR_NOMEM, "plan: host allocation failed");
+        }
+    }
+    DeviceGuard g(c->device);
+    if (!g.ok) return set_err(c, FGI_ERR_CUDA, "cudaSetDevice failed");
+    c->precision = precision;
+    try {
+        return build_plan(c, tune_cache_path);
+    } catch (const std::bad_alloc &) {
+        return set_err(c, FGI_ERR_NOMEM, "plan: host allocation failed");
+    }
+}
+
+int fgi_set_precision(fgi_ctx *c, fgi_precision precision)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (precision != FGI_FP64 && precision != FGI_SPLIT_BF16 && precision != FGI_BF16)
+        return set_err(c, FGI_ERR_ARG, "unknown precision %d", (int)precision);
+    c->precision = precision;
+    return FGI_OK;
+}
+
+int fgi_get_sizes(fgi_ctx *c, int64_t *n_fn, int64_t *nnz, int64_t *n_pts, int64_t *n_atoms)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (n_fn) *n_fn = c->n_fn;
+    if (nnz) *nnz = c->nnz;
+    if (n_pts) *n_pts = c->n_pts;
+    if (n_atoms) *n_atoms = (int64_t)c->atom_species.size();
+    return FGI_OK;
+}
+
+int fgi_get_system(fgi_ctx *c, int sys, int64_t *fn0, int64_t *n_fn, int64_t *val0, int64_t *nnz)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (sys < 0 || sys >= c->n_sys) return set_err(c, FGI_ERR_ARG, "system %d out of range", sys);
+    if (fn0) *fn0 = c->sys_fn0[sys];
+    if (n_fn) *n_fn = c->sys_nfn[sys];
+    if (val0) *val0 = c->sys_val0[sys];
+    if (nnz) *nnz = c->sys_nnz[sys];
+    return FGI_OK;
+}
+
+int fgi_get_pattern(fgi_ctx *c, int sys, int64_t *nnz, const int64_t **rowptr, const int **col)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (sys < 0 || sys >= c->n_sys) return set_err(c, FGI_ERR_ARG, "system %d out of range", sys);
+    if (c->pattern_sys != sys) {
+        try {
+            const int64_t nf = c->sys_nfn[sys], f0 = c->sys_fn0[sys], v0 = c->sys_val0[sys];
+            c->pat_rowptr.assign(nf + 1, 0);
+            c->pat_col.assign(c->sys_nnz[sys], 0);
+            for (int64_t a = c->atom_off[sys]; a < c->atom_off[sys + 1]; a++) {
+                for (int li = 0; li < c->atom_nfn[a]; li++) {
+                    const long long gi = c->atom_fn0[a] + li;
+                    long long k = c->rowptr[gi] - v0;
+                    c->pat_rowptr[gi - f0] = k;
+                    for (long long j = gi; j < c->atom_fn0[a] + c->atom_nfn[a]; j++) c->pat_col[k++] = (int)(j - f0);
+                    for (int b : c->nbr[a]) {
+                        if (b == a) continue;
+                        for (int lj = 0; lj < c->atom_nfn[b]; lj++) c->pat_col[k++] = (int)(c->atom_fn0[b] + lj - f0);
+                    }
+                }
+            }
+            c->pat_rowptr[nf] = c->sys_nnz[sys];
+            c->pattern_sys = sys;
+        } catch (const std::bad_alloc &) {
+            c->pattern_sys = -1;
+            return set_err(c, FGI_ERR_NOMEM, "pattern: host allocation failed");
+        }
+    }
+    if (nnz) *nnz = c->sys_nnz[sys];
+    if (rowptr) *rowptr = c->pat_rowptr.data();
+    if (col) *col = c->pat_col.data();
+    return FGI_OK;
+}
+
+int fgi_workspace_size(fgi_ctx *c, size_t *bytes)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (!bytes) return set_err(c, FGI_ERR_ARG, "bytes is NULL");
+    *bytes = workspace_need(c);
+    return FGI_OK;
+}
+
+int fgi_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void *ws, size_t ws_bytes,
+                    void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!v || !h) return set_err(c, FGI_ERR_ARG, "v or h is NULL");
+    if ((rc = check_ws(c, ws, ws_bytes))) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!accumulate) CUDA_TRY(c, cudaMemsetAsync(h, 0, (size_t)c->nnz * sizeof(double), s));
+    if (c->precision == FGI_FP64) {
+        DevPlan P = c->dp;
+        P.batches = c->d_batches_f64;
+        for (const Wave &w : c->waves) {
+            {
+                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+                CUDA_TRY(c, launch_phi_f64(P, w.b0, w.nb, (double *)ws, s));
+            }
+            ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
+            CUDA_TRY(c, launch_h_f64(P, c->d_items + w.it0, (int)w.nit, (const double *)ws, v, h, s));
+        }
+        return FGI_OK;
+    }
+    std::string terr;
+    rc = tc_integrate_h(c->tc, c->dp, c->precision == FGI_SPLIT_BF16 ? 3 : 1, v, h, ws, s, &terr);
+    if (rc) return set_err(c, rc, "%s", terr.c_str());
+    return FGI_OK;
+}
+
+int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws, size_t ws_bytes,
+                void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!d || !n) return set_err(c, FGI_ERR_ARG, "d or n is NULL");
+    if ((rc = check_ws(c, ws, ws_bytes))) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaMemsetAsync(n, 0, (size_t)c->n_pts * sizeof(double), s));
+    DevPlan P = c->dp;
+    P.batches = c->d_batches_f64;
+    if (c->precision == FGI_FP64) {
+        for (const Wave &w : c->waves) {
+            {
+                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+                CUDA_TRY(c, launch_phi_f64(P, w.b0, w.nb, (double *)ws, s));
+            }
+            ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
+            CUDA_TRY(c, launch_density_f64(P, c->d_items + w.dt0, (int)w.ndt, (const double *)ws, d, 1.0, n,
+                                           nullptr, s));
+        }
+    } else {
+        std::string terr;
+        rc = tc_density(c->tc, c->dp, c->precision == FGI_SPLIT_BF16 ? 3 : 1, d, 1.0, n, ws, s, &terr);
+        if (rc) return set_err(c, rc, "%s", terr.c_str());
+    }
+    if (traces) {
+        CUDA_TRY(c, cudaMemsetAsync(traces, 0, (size_t)c->n_sys * sizeof(double), s));
+        ProfScope ps(c, s, 4, 2.0 * c->n_pts, 16.0 * c->n_pts);
+        CUDA_TRY(c, launch_point_traces(P, (int)c->batch_sys.size(), n, traces, s));
+    }
+    return FGI_OK;
+}
+
+int fgi_adjoint(fgi_ctx *c, const double *gv, const double *v, double *dv, double *dR, void *ws,
+                size_t ws_bytes, void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!gv || !v || !dv || !dR) return set_err(c, FGI_ERR_ARG, "NULL argument");
+    if ((rc = check_ws(c, ws, ws_bytes))) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaMemsetAsync(dv, 0, (size_t)c->n_pts * sizeof(double), s));
+    CUDA_TRY(c, cudaMemsetAsync(dR, 0, c->atom_species.size() * 3 * sizeof(double), s));
+    DevPlan P = c->dp;
+    P.batches = c->d_batches_f64;
+    size_t max_elems = 0;
+    for (const Wave &w : c->waves) max_elems = std::max(max_elems, w.ws_elems);
+    double *phi_ws = (double *)ws;
+    double *e_ws = phi_ws + max_elems;
+    for (const Wave &w : c->waves) {
+        {
+            ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+            CUDA_TRY(c, launch_phi_f64(P, w.b0, w.nb, phi_ws, s));
+        }
+        {
+            ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
+            CUDA_TRY(c, launch_density_f64(P, c->d_items + w.dt0, (int)w.ndt, phi_ws, gv, 0.5, dv, e_ws, s));
+        }
+        ProfScope ps(c, s, 3, 40.0 * w.phi_flops / 30.0, w.phi_bytes);
+        CUDA_TRY(c, launch_adjoint_grad(P, w.b0, w.nb, e_ws, v, dR, s));
+    }
+    CUDA_TRY(c, launch_scale_by_weight(P, c->n_pts, dv, s));
+    return FGI_OK;
+}
+
+int fgi_trace(fgi_ctx *c, const double *a, const double *b, double *out, void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!a || !b || !out) return set_err(c, FGI_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, cudaMemsetAsync(out, 0, (size_t)c->n_sys * sizeof(double), s));
+    if (c->n_fn > 0)
+        CUDA_TRY(c, launch_matrix_trace(c->dp, c->n_sys, c->d_sys_fn0, c->d_sys_val0, c->n_fn, c->nnz, c->d_fn_sys,
+                                        a, b, out, s));
+    return FGI_OK;
+}
+
+int fgi_sync(fgi_ctx *c, void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    CUDA_TRY(c, cudaStreamSynchronize((cudaStream_t)stream));
+    int st = 0;
+    CUDA_TRY(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (st & kStatusTimeout) return set_err(c, FGI_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (st & kStatusNonFinite) return set_err(c, FGI_ERR_NONFINITE, "non-finite value in an input");
+    if (st & kStatusBadIndex) return set_err(c, FGI_ERR_CUDA, "device index check failed");
+    return FGI_OK;
+}
+
+int fgi_profile(fgi_ctx *c, int enable)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    if (enable) {
+        while (c->ev_pool.size() < 16384) {
+            cudaEvent_t e;
+            CUDA_TRY(c, cudaEventCreate(&e));
+            c->ev_pool.push_back(e);
+        }
+    }
+    c->prof_on = enable != 0;
+    c->ev_used = 0;
+    c->recs.clear();
+    c->prof_dropped = 0;
+    return FGI_OK;
+}
+
+int fgi_profile_read(fgi_ctx *c, int kind, int64_t *launches, double *ms, double *flops, double *bytes)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (kind < 0 || kind > 4) return set_err(c, FGI_ERR_ARG, "kernel kind %d out of range", kind);
+    DeviceGuard g(c->device);
+    long long n = 0;
+    double t = 0, f = 0, by = 0;
+    for (const ProfRec &r : c->recs) {
+        if (r.kind != kind) continue;
+        CUDA_TRY(c, cudaEventSynchronize(r.b));
+        float e = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&e, r.a, r.b));
+        n++;
+        t += e;
+        f += r.flops;
+        by += r.bytes;
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (flops) *flops = f;
+    if (bytes) *bytes = by;
+    if (c->prof_dropped) return set_err(c, FGI_ERR_ARG, "profile event pool exhausted (%lld launches not timed)",
+                                        c->prof_dropped);
+    return FGI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal plan structures shared by the host runtime and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fgi {
+
+constexpr int kMaxL = 3;
+constexpr int kMaxBatchPoints = 1024;
+constexpr int kMaxBatchFns = 8192;       // per-batch local-function tables live in shared memory
+constexpr int kImgRows = 128;            // tcgen05 operand image: rows (functions) per tile
+constexpr int kImgCols = 64;             // points per 128-byte swizzle row
+
+// status word bits (device)
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusNonFinite = 2;
+constexpr int kStatusBadIndex = 4;
+
+struct DevRadial {
+    double h, inv_h, rcut;
+    long long coef_off;   // in units of 4 coefficients (one interval)
+    int nk, l;
+};
+
+struct DevSpecies {
+    int shell0;           // first entry in shell_rad[]
+    int n_shell;
+    int n_fn;
+    int pad;
+    double rcut;          // largest cutoff of the species' radials
+};
+
+struct DevBatch {
+    long long pt0;        // first point (global)
+    int np;               // points in the batch
+    int sys;              // system
+    int act0;             // first active-atom entry
+    int n_act;            // active atoms
+    int nfn;              // active functions n_b
+    int kpad;             // padded point count used by the operand layouts
+    long long ws_off;     // element offset of the batch's operand block in the wave's workspace
+};
+
+struct DevAct {
+    int atom;             // global atom index
+    int fn_loc;           // first local function of this atom in the batch
+};
+
+struct WorkItem {         // one tile of a per-batch contraction
+    int batch;
+    short ti, tj;
+};
+
+struct DevPlan {
+    // points (SoA) and weights
+    const double *px, *py, *pz, *pw;
+    // atoms
+    const double *atom_xyz;       // [n_atoms][3]
+    const int *atom_species;
+    const long long *atom_fn0;    // global index of the atom's first function
+    const int *atom_loc;          // index of the atom inside its system
+    // basis
+    const DevSpecies *species;
+    const int *shell_rad;         // radial id per species shell
+    const DevRadial *radials;
+    const double *coef;           // [sum intervals][4] FP64
+    const float *coef32;          // the same in FP32
+    // systems
+    const int *sys_nat;           // atoms per system
+    const long long *sys_pair_off;// offset of the system's pairpos table
+    const int *pairpos;           // [nat*nat] per system: position of atom b's run in atom a's row, -1 absent
+    const long long *rowptr;      // per global function: index of its first stored value
+    // batches
+    const DevBatch *batches;
+    const DevAct *act;
+    int *status;
+};
+
+// ---- launchers (return the launch status) ----
+// FP64 path
+cudaError_t launch_phi_f64(const DevPlan &P, int b0, int nb, double *ws, cudaStream_t s);
+cudaError_t launch_h_f64(const DevPlan &P, const WorkItem *items, int n_items, const double *ws,
+                         const double *v, double *h, cudaStream_t s);
+cudaError_t launch_density_f64(const DevPlan &P, const WorkItem *items, int n_items,
+                               const double *ws, const double *d, double offdiag_scale,
+                               double *n_out, double *e_out, cudaStream_t s);
+cudaError_t launch_adjoint_grad(const DevPlan &P, int b0, int nb, const double *e_ws,
+                                const double *v, double *dR, cudaStream_t s);
+// shared helpers
+cudaError_t launch_scale_by_weight(const DevPlan &P, long long n_pts, double *x, cudaStream_t s);
+cudaError_t launch_point_traces(const DevPlan &P, int n_batch, const double *n, double *traces,
+                                cudaStream_t s);
+cudaError_t launch_matrix_trace(const DevPlan &P, int n_sys, const long long *sys_fn0,
+                                const long long *sys_val0, long long n_fn_total,
+                                long long nnz_total, const int *fn_sys, const double *a,
+                                const double *b, double *out, cudaStream_t s);
+cudaError_t launch_check_finite(const DevPlan &P, const double *x, long long n, cudaStream_t s);
+
+}  // namespace fgi

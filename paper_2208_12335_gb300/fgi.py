@@ -1,0 +1,313 @@
+"""Python binding of the C ABI in ``include/fgi.h`` (argument marshalling only).
+
+Every step of the computation runs in ``libfgi.so`` on the GPU; this module
+only converts arrays and tensors to pointers.  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the library is missing,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfgi.so")
+
+FGI_FP64, FGI_SPLIT_BF16, FGI_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FGI_FP64, "split_bf16": FGI_SPLIT_BF16, "bf16": FGI_BF16}
+ERRORS = {-1: "FGI_ERR_ARG", -2: "FGI_ERR_STATE", -3: "FGI_ERR_CUDA", -4: "FGI_ERR_WORKSPACE",
+          -5: "FGI_ERR_TIMEOUT", -6: "FGI_ERR_NONFINITE", -7: "FGI_ERR_UNSUPPORTED",
+          -8: "FGI_ERR_NOMEM"}
+
+SYMBOLS = ["fgi_create", "fgi_destroy", "fgi_last_error", "fgi_add_radial", "fgi_add_species",
+           "fgi_set_systems", "fgi_set_grid", "fgi_plan", "fgi_set_precision", "fgi_get_sizes",
+           "fgi_get_system", "fgi_get_pattern", "fgi_workspace_size", "fgi_integrate_h",
+           "fgi_density", "fgi_adjoint", "fgi_trace", "fgi_sync", "fgi_profile",
+           "fgi_profile_read"]
+KERNEL_KINDS = {"basis": 0, "h": 1, "density": 2, "adjoint": 3, "other": 4}
+
+
+class FGIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERRORS.get(code, code), msg))
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError("libfgi.so is not built (run __graft_entry__.build()); "
+                          "there is no fallback path")
+    lib = C.CDLL(path)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "fgi_create": ([C.POINTER(P), I], I),
+        "fgi_destroy": ([P], I),
+        "fgi_last_error": ([P], C.c_char_p),
+        "fgi_add_radial": ([P, I, D, I, P, C.POINTER(I)], I),
+        "fgi_add_species": ([P, D, I, P, C.POINTER(I)], I),
+        "fgi_set_systems": ([P, I, P, P, P], I),
+        "fgi_set_grid": ([P, I64, P, P, I64, P, P], I),
+        "fgi_plan": ([P, I, C.c_char_p], I),
+        "fgi_set_precision": ([P, I], I),
+        "fgi_get_sizes": ([P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)], I),
+        "fgi_get_system": ([P, I, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)], I),
+        "fgi_get_pattern": ([P, I, C.POINTER(I64), C.POINTER(P), C.POINTER(P)], I),
+        "fgi_workspace_size": ([P, C.POINTER(C.c_size_t)], I),
+        "fgi_integrate_h": ([P, P, P, I, P, C.c_size_t, P], I),
+        "fgi_density": ([P, P, P, P, P, C.c_size_t, P], I),
+        "fgi_adjoint": ([P, P, P, P, P, P, C.c_size_t, P], I),
+        "fgi_trace": ([P, P, P, P, P], I),
+        "fgi_sync": ([P, P], I),
+        "fgi_profile": ([P, I], I),
+        "fgi_profile_read": ([P, I, C.POINTER(I64), C.POINTER(D), C.POINTER(D), C.POINTER(D)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dev_f64(t, n, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("%s must be a CUDA float64 tensor" % name)
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be contiguous with %d elements" % (name, n))
+    return t
+
+
+class Context:
+    """One library context: inputs, plan, and the compute calls."""
+
+    def __init__(self, device: int = 0):
+        self._lib = lib()
+        self._h = C.c_void_p()
+        self.device = device
+        rc = self._lib.fgi_create(C.byref(self._h), device)
+        if rc != 0:
+            raise FGIError(rc, "fgi_create(device=%d)" % device)
+        self._keep = []
+        self._ws = None
+
+    def close(self):
+        if self._h:
+            self._lib.fgi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise FGIError(rc, self._lib.fgi_last_error(self._h).decode())
+
+    # ---- inputs
+    def add_radial(self, l: int, h: float, coef) -> int:
+        coef = _np(coef, np.float64)
+        out = C.c_int()
+        self._check(self._lib.fgi_add_radial(self._h, int(l), float(h), coef.shape[0] + 1, _ptr(coef),
+                                             C.byref(out)))
+        return out.value
+
+    def add_species(self, Z: float, radial_ids) -> int:
+        ids = _np(radial_ids, np.int32)
+        out = C.c_int()
+        self._check(self._lib.fgi_add_species(self._h, float(Z), len(ids), _ptr(ids), C.byref(out)))
+        return out.value
+
+    def set_systems(self, atom_off, species, xyz):
+        atom_off = _np(atom_off, np.int64)
+        species = _np(species, np.int32)
+        xyz = _np(xyz, np.float64)
+        self._check(self._lib.fgi_set_systems(self._h, len(atom_off) - 1, _ptr(atom_off), _ptr(species),
+                                              _ptr(xyz)))
+
+    def set_grid(self, xyz, w, batch_off, batch_sys):
+        xyz = _np(xyz, np.float64)
+        w = _np(w, np.float64)
+        batch_off = _np(batch_off, np.int64)
+        batch_sys = _np(batch_sys, np.int32)
+        self._check(self._lib.fgi_set_grid(self._h, len(w), _ptr(xyz), _ptr(w), len(batch_off) - 1,
+                                           _ptr(batch_off), _ptr(batch_sys)))
+
+    def plan(self, precision="fp64", tune_path=None):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(self._lib.fgi_plan(self._h, p, tune_path.encode() if tune_path else None))
+        self._ws = None
+
+    def set_precision(self, precision):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(self._lib.fgi_set_precision(self._h, p))
+
+    def load(self, problem, precision="fp64", tune_path=None):
+        """Marshal a problem object (radials, species, systems, grid) and plan."""
+        rid = [self.add_radial(r.l, r.h, r.coef) for r in problem.radials]
+        for sp in problem.species:
+            self.add_species(sp.Z, [rid[k] for k in sp.radial_ids])
+        self.set_systems(problem.atom_off, problem.atom_species, problem.atom_xyz)
+        self.set_grid(problem.pts, problem.w, problem.batch_off, problem.batch_sys)
+        self.plan(precision, tune_path)
+        return self
+
+    # ---- queries
+    def sizes(self):
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self._lib.fgi_get_sizes(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)       # n_fn, nnz, n_pts, n_atoms
+
+    def system(self, s: int):
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self._lib.fgi_get_system(self._h, s, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)       # fn0, n_fn, val0, nnz
+
+    def pattern(self, s: int = 0):
+        nnz = C.c_int64()
+        rp = C.c_void_p()
+        col = C.c_void_p()
+        self._check(self._lib.fgi_get_pattern(self._h, s, C.byref(nnz), C.byref(rp), C.byref(col)))
+        n_fn = self.system(s)[1]
+        rowptr = np.ctypeslib.as_array(C.cast(rp, C.POINTER(C.c_int64)), shape=(n_fn + 1,)).copy()
+        cols = (np.ctypeslib.as_array(C.cast(col, C.POINTER(C.c_int32)), shape=(nnz.value,)).copy()
+                if nnz.value else np.zeros(0, np.int32))
+        return rowptr, cols
+
+    def workspace_size(self) -> int:
+        b = C.c_size_t()
+        self._check(self._lib.fgi_workspace_size(self._h, C.byref(b)))
+        return b.value
+
+    def workspace(self):
+        need = self.workspace_size()
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda:%d" % self.device)
+        return self._ws
+
+    # ---- compute
+    def integrate_h(self, v, h=None, accumulate=False, ws=None, stream=None):
+        n_fn, nnz, n_pts, _ = self.sizes()
+        v = _dev_f64(v, n_pts, "v")
+        if h is None:
+            h = torch.empty(nnz, dtype=torch.float64, device=v.device)
+        _dev_f64(h, nnz, "h")
+        ws = self.workspace() if ws is None else ws
+        self._check(self._lib.fgi_integrate_h(self._h, _ptr(v), _ptr(h), int(bool(accumulate)), _ptr(ws),
+                                              ws.numel() * ws.element_size(), _stream(stream)))
+        return h
+
+    def density(self, d, n=None, traces=None, ws=None, stream=None, with_traces=True):
+        n_fn, nnz, n_pts, _ = self.sizes()
+        d = _dev_f64(d, nnz, "d")
+        if n is None:
+            n = torch.empty(n_pts, dtype=torch.float64, device=d.device)
+        _dev_f64(n, n_pts, "n")
+        n_sys = len(self._sys_list())
+        if traces is None and with_traces:
+            traces = torch.empty(n_sys, dtype=torch.float64, device=d.device)
+        ws = self.workspace() if ws is None else ws
+        self._check(self._lib.fgi_density(self._h, _ptr(d), _ptr(n), _ptr(traces), _ptr(ws),
+                                          ws.numel() * ws.element_size(), _stream(stream)))
+        return n, traces
+
+    def adjoint(self, g, v, dv=None, dR=None, ws=None, stream=None):
+        n_fn, nnz, n_pts, n_at = self.sizes()
+        g = _dev_f64(g, nnz, "g")
+        v = _dev_f64(v, n_pts, "v")
+        if dv is None:
+            dv = torch.empty(n_pts, dtype=torch.float64, device=g.device)
+        if dR is None:
+            dR = torch.empty((n_at, 3), dtype=torch.float64, device=g.device)
+        ws = self.workspace() if ws is None else ws
+        self._check(self._lib.fgi_adjoint(self._h, _ptr(g), _ptr(v), _ptr(dv), _ptr(dR), _ptr(ws),
+                                          ws.numel() * ws.element_size(), _stream(stream)))
+        return dv, dR
+
+    def trace(self, a, b, out=None, stream=None):
+        _, nnz, _, _ = self.sizes()
+        _dev_f64(a, nnz, "a")
+        _dev_f64(b, nnz, "b")
+        if out is None:
+            out = torch.empty(len(self._sys_list()), dtype=torch.float64, device=a.device)
+        self._check(self._lib.fgi_trace(self._h, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
+        return out
+
+    def sync(self, stream=None):
+        self._check(self._lib.fgi_sync(self._h, _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.fgi_profile(self._h, int(bool(enable))))
+
+    def profile_read(self, kind):
+        k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        n = C.c_int64()
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.fgi_profile_read(self._h, k, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+        return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+
+    def _sys_list(self):
+        out = []
+        s = 0
+        while True:
+            rc = self._lib.fgi_get_system(self._h, s, None, None, None, None)
+            if rc != 0:
+                break
+            out.append(s)
+            s += 1
+        return out
+
+
+class HIntegrate(torch.autograd.Function):
+    """h = H(v, R) as a differentiable function of the potential on the grid
+    and of the atom positions (at the planned geometry).  The backward pass
+    calls the adjoint kernels, which recompute the basis per batch."""
+
+    @staticmethod
+    def forward(fctx, context: Context, v, R):
+        fctx.context = context
+        fctx.save_for_backward(v)
+        return context.integrate_h(v.detach().contiguous())
+
+    @staticmethod
+    def backward(fctx, g):
+        (v,) = fctx.saved_tensors
+        dv, dR = fctx.context.adjoint(g.contiguous(), v.detach().contiguous())
+        return None, dv, dR
+
+
+def integrate(context: Context, v, R):
+    return HIntegrate.apply(context, v, R)

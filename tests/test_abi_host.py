@@ -1,0 +1,178 @@
+"""Host-side tests of the C ABI (no GPU): exported symbols, argument and
+state errors, the sparsity pattern, and plan tables of host-only contexts."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fgi():
+    from paper_2208_12335_gb300 import build as B
+    B.build()
+    import paper_2208_12335_gb300 as P
+    return P
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "fgi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgi_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(fgi):
+    lib = C.CDLL(fgi.LIB_PATH)
+    names = header_symbols()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(fgi.SYMBOLS) == sorted(n for n in names if n in fgi.SYMBOLS)
+    assert set(fgi.SYMBOLS) <= set(names)
+
+
+def host_ctx(fgi, prob, precision="fp64"):
+    ctx = fgi.Context.__new__(fgi.Context)
+    ctx._lib = fgi.lib()
+    ctx._h = C.c_void_p()
+    ctx.device = -1
+    ctx._keep = []
+    ctx._ws = None
+    rc = ctx._lib.fgi_create(C.byref(ctx._h), -1)
+    assert rc == 0
+    return ctx.load(prob, precision)
+
+
+@pytest.fixture(scope="module")
+def water():
+    return W.tiny_water(n_rad=16, n_ang=26)
+
+
+def test_host_only_plan_sizes_and_pattern(fgi, water):
+    ctx = host_ctx(fgi, water)
+    n_fn, nnz, n_pts, n_at = ctx.sizes()
+    assert (n_fn, n_pts, n_at) == (7, water.n_pts, 3)
+    # all three atoms are within each other's cutoffs: dense upper triangle
+    assert nnz == 7 * 8 // 2
+    rowptr, col = ctx.pattern(0)
+    for i in range(7):
+        assert list(col[rowptr[i]:rowptr[i + 1]]) == list(range(i, 7))
+    assert ctx.workspace_size() > 0
+
+
+def _pattern_reference(prob, s=0):
+    """Stored pairs from the definition: atoms closer than the sum of their
+    largest cutoffs (upper triangle, row-major, columns ascending)."""
+    a0, a1 = prob.atom_off[s], prob.atom_off[s + 1]
+    sp = prob.atom_species[a0:a1]
+    xyz = prob.atom_xyz[a0:a1]
+    rc = np.array([max(prob.radials[r].r_cut for r in prob.species[k].radial_ids) for k in sp])
+    nf = np.array(prob.fns_per_species())[sp]
+    fn0 = np.concatenate([[0], np.cumsum(nf)])
+    owner = np.repeat(np.arange(len(sp)), nf)
+    d = np.linalg.norm(xyz[:, None] - xyz[None], axis=2)
+    near = d < rc[:, None] + rc[None, :]
+    rows = []
+    for i in range(fn0[-1]):
+        a = owner[i]
+        cols = [j for j in range(i, fn0[-1]) if near[a, owner[j]] or owner[j] == a]
+        rows.append(cols)
+    return rows
+
+
+def test_pattern_matches_definition_on_a_sparse_cluster(fgi):
+    prob = W.chno_cluster(n_atoms=60, n_rad=8, n_ang=14, atoms_with_grid=[0, 1, 2])
+    ctx = host_ctx(fgi, prob)
+    rowptr, col = ctx.pattern(0)
+    ref = _pattern_reference(prob)
+    assert len(rowptr) == len(ref) + 1
+    assert rowptr[-1] < len(ref) * (len(ref) + 1) // 2      # genuinely sparse
+    for i, cols in enumerate(ref):
+        assert list(col[rowptr[i]:rowptr[i + 1]]) == cols
+
+
+def test_many_systems_layout(fgi):
+    parts = [W.tiny_water(n_rad=8, n_ang=14), W.tiny_water(n_rad=10, n_ang=14)]
+    prob = W.merge_problems("two", parts, 0)
+    ctx = host_ctx(fgi, prob)
+    assert ctx.system(0) == (0, 7, 0, 28)
+    assert ctx.system(1) == (7, 7, 28, 28)
+    assert ctx.sizes()[:2] == (14, 56)
+
+
+def test_argument_and_state_errors(fgi, water):
+    lib = fgi.lib()
+    h = C.c_void_p()
+    assert lib.fgi_create(C.byref(h), -1) == 0
+    try:
+        # compute before plan
+        assert lib.fgi_integrate_h(h, None, None, 0, None, 0, None) == -2
+        # l out of range
+        coef = np.zeros((3, 4))
+        rid = C.c_int()
+        assert lib.fgi_add_radial(h, 4, 0.1, 4, coef.ctypes.data_as(C.c_void_p), C.byref(rid)) == -7
+        assert b"l = 4" in lib.fgi_last_error(h)
+        # non-finite coefficients
+        coef[1, 2] = np.nan
+        assert lib.fgi_add_radial(h, 0, 0.1, 4, coef.ctypes.data_as(C.c_void_p), C.byref(rid)) == -6
+        # NULL coefficients, bad knot count
+        assert lib.fgi_add_radial(h, 0, 0.1, 4, None, C.byref(rid)) == -1
+        assert lib.fgi_add_radial(h, 0, 0.1, 1, coef.ctypes.data_as(C.c_void_p), C.byref(rid)) == -1
+        # species with an unknown radial
+        ids = np.array([5], dtype=np.int32)
+        assert lib.fgi_add_species(h, 1.0, 1, ids.ctypes.data_as(C.c_void_p), C.byref(rid)) == -1
+        # plan without inputs
+        assert lib.fgi_plan(h, 0, None) == -2
+    finally:
+        lib.fgi_destroy(h)
+
+
+def test_grid_errors(fgi, water):
+    ctx = host_ctx(fgi, water)
+    big = np.zeros((1100, 3))
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.set_grid(big, np.ones(1100), [0, 1100], [0])
+    assert e.value.code == -1
+    bad = water.pts.copy()
+    bad[3, 1] = np.inf
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.set_grid(bad, water.w, water.batch_off, water.batch_sys)
+    assert e.value.code == -6
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.set_grid(water.pts, water.w, water.batch_off[:-1], water.batch_sys[:-1])
+    assert e.value.code == -1
+    # batch referring to a missing system is caught at plan time
+    ctx.set_grid(water.pts, water.w, water.batch_off, np.full(water.n_batch, 3, np.int32))
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("fp64")
+    assert e.value.code == -1
+
+
+def test_host_only_context_refuses_compute_and_checks_precision(fgi, water):
+    ctx = host_ctx(fgi, water)
+    lib = fgi.lib()
+    assert lib.fgi_sync(ctx._h, None) == -2
+    assert lib.fgi_density(ctx._h, None, None, None, None, 0, None) == -2
+    with pytest.raises(fgi.FGIError):
+        ctx.set_precision(7)
+    ctx.set_precision("split_bf16")
+
+
+def test_empty_batches_and_far_points_plan(fgi):
+    """A batch whose points are beyond every cutoff has no active functions."""
+    prob = W.tiny_water(n_rad=8, n_ang=14)
+    far = np.array([[100.0, 0, 0], [100.0, 1.0, 0]])
+    pts = np.concatenate([prob.pts, far])
+    w = np.concatenate([prob.w, [1.0, 1.0]])
+    boff = np.concatenate([prob.batch_off, [prob.n_pts + 2]])
+    bsys = np.concatenate([prob.batch_sys, [0]])
+    prob2 = W.Problem("far", prob.radials, prob.species, prob.atom_off, prob.atom_species,
+                      prob.atom_xyz, pts, w, boff.astype(np.int64), bsys.astype(np.int32),
+                      np.concatenate([prob.v, [0.0, 0.0]]))
+    ctx = host_ctx(fgi, prob2)
+    assert ctx.sizes()[2] == prob.n_pts + 2

@@ -1,0 +1,215 @@
+"""GPU-vs-oracle parity through the C ABI.
+
+The CUDA path and the FP64 oracle run on the same seeded inputs; results
+are compared element by element on the stored pattern (H), point by point
+(density, dL/dv) and atom by atom (dL/dR).  Tolerances:
+
+* FP64 path: 1e-11 relative to max|H| (rounding order only).
+* split BF16: max |dH_ij| <= 1e-7 Ha and density relative L2 <= 1e-7 (the
+  accuracy targets the method sets for the split contractions).
+* plain BF16: max |dH_ij| <= 5e-3 Ha (reported, a sanity bound only).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+TOL_SPLIT_H = 1e-7
+TOL_SPLIT_N = 1e-7
+TOL_BF16_H = 5e-3
+
+
+@pytest.fixture(scope="module")
+def fgi():
+    from paper_2208_12335_gb300 import build as B
+    B.build()
+    import paper_2208_12335_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return P
+
+
+def rows_cols(ctx, s=0):
+    rowptr, col = ctx.pattern(s)
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    return rows, col
+
+
+def stored(ctx, M, s=0):
+    r, c = rows_cols(ctx, s)
+    return M[r, c]
+
+
+def dense_sym(ctx, vals, n, s=0, offdiag=1.0):
+    r, c = rows_cols(ctx, s)
+    M = np.zeros((n, n))
+    M[r, c] = vals * np.where(r == c, 1.0, offdiag)
+    M[c, r] = vals * np.where(r == c, 1.0, offdiag)
+    return M
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def water():
+    prob = W.tiny_water()
+    B = O.system_basis(prob)
+    return prob, B, O.h_matrix(B, prob.pts, prob.w, prob.v), O.h_matrix(B, prob.pts, prob.w)
+
+
+PRECISIONS = [("fp64", None), ("split_bf16", TOL_SPLIT_H), ("bf16", TOL_BF16_H)]
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_tiny_water(fgi, water, precision, tol):
+    prob, B, H, _ = water
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()
+    ref = stored(ctx, H)
+    err = np.max(np.abs(h - ref))
+    bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
+    assert err <= bound, (precision, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", None), ("split_bf16", TOL_SPLIT_N)])
+def test_density_and_electron_count_tiny_water(fgi, water, precision, tol):
+    prob, B, _, S = water
+    rng = W.rng_for(0, W.PURPOSE_D)
+    q, _ = np.linalg.qr(rng.standard_normal((B.n_fn, 5)))
+    ev, U = np.linalg.eigh(S)
+    C_ = U @ np.diag(ev ** -0.5) @ U.T @ q
+    D = 2.0 * C_ @ C_.T
+    ctx = fgi.Context(0).load(prob, precision)
+    n, tr = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    n = n.cpu().numpy()
+    nref = O.density(B, prob.pts, D)
+    rel = np.linalg.norm(n - nref) / np.linalg.norm(nref)
+    assert rel <= (1e-12 if tol is None else tol), rel
+    assert tr.cpu().numpy()[0] == pytest.approx(10.0, rel=1e-10 if tol is None else 1e-6)
+    # tr(DS) through the trace kernel, with S from the same library
+    ctx.set_precision("fp64")
+    s_vals = ctx.integrate_h(dev(np.ones(prob.n_pts)))
+    t = ctx.trace(dev(stored(ctx, D)), s_vals).cpu().numpy()[0]
+    assert t == pytest.approx(10.0, rel=1e-10)
+
+
+def test_adjoint_tiny_water_fp64(fgi, water):
+    prob, B, _, _ = water
+    ctx = fgi.Context(0).load(prob, "fp64")
+    rng = W.rng_for(0, W.PURPOSE_G)
+    g = rng.standard_normal(ctx.sizes()[1])
+    dv, dR = ctx.adjoint(dev(g), dev(prob.v))
+    ctx.sync()
+    G = dense_sym(ctx, g, B.n_fn, offdiag=0.5)
+    dv_ref, dR_ref = O.adjoint(B, prob.pts, prob.w, prob.v, G)
+    np.testing.assert_allclose(dv.cpu().numpy(), dv_ref, rtol=0, atol=1e-12 * np.abs(dv_ref).max())
+    np.testing.assert_allclose(dR.cpu().numpy(), dR_ref, rtol=0, atol=1e-11 * np.abs(dR_ref).max())
+
+
+def test_autograd_function_matches_oracle(fgi, water):
+    prob, B, _, _ = water
+    ctx = fgi.Context(0).load(prob, "fp64")
+    v = dev(prob.v).requires_grad_(True)
+    R = dev(prob.atom_xyz).requires_grad_(True)
+    h = fgi.integrate(ctx, v, R)
+    rng = W.rng_for(0, W.PURPOSE_G)
+    g = dev(rng.standard_normal(h.numel()))
+    (h * g).sum().backward()
+    G = dense_sym(ctx, g.cpu().numpy(), B.n_fn, offdiag=0.5)
+    dv_ref, dR_ref = O.adjoint(B, prob.pts, prob.w, prob.v, G)
+    np.testing.assert_allclose(v.grad.cpu().numpy(), dv_ref, rtol=0, atol=1e-12 * np.abs(dv_ref).max())
+    np.testing.assert_allclose(R.grad.cpu().numpy(), dR_ref, rtol=0, atol=1e-11 * np.abs(dR_ref).max())
+
+
+@pytest.fixture(scope="module")
+def si64_sub():
+    full = W.si64()
+    rng = np.random.default_rng(123)
+    ids = np.sort(rng.choice(full.n_batch, size=24, replace=False))
+    prob = full.subgrid(ids)
+    B = O.system_basis(prob)
+    sub = O.active_functions(B, prob.pts)
+    H = O.h_matrix(B, prob.pts, prob.w, prob.v, sub=sub)
+    return prob, B, sub, H
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_si64_subgrid(fgi, si64_sub, precision, tol):
+    prob, B, sub, Hs = si64_sub
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()
+    r, c = rows_cols(ctx)
+    pos = -np.ones(B.n_fn, dtype=np.int64)
+    pos[sub] = np.arange(len(sub))
+    inside = (pos[r] >= 0) & (pos[c] >= 0)
+    ref = np.zeros(len(h))
+    ref[inside] = Hs[pos[r[inside]], pos[c[inside]]]
+    err = np.max(np.abs(h - ref))
+    bound = TOL_FP64 * np.abs(Hs).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(Hs).max())
+    assert np.all(h[~inside] == 0.0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split_bf16", TOL_SPLIT_N)])
+def test_density_si64_subgrid(fgi, si64_sub, precision, tol):
+    prob, B, sub, _ = si64_sub
+    ctx = fgi.Context(0).load(prob, precision)
+    rng = W.rng_for(1, W.PURPOSE_D)
+    D, _ = W.density_matrix_occ(B.n_fn, 448, rng)
+    n, _ = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    nref = O.density(B, prob.pts, D[np.ix_(sub, sub)], sub=sub)
+    rel = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
+    assert rel <= tol, rel
+
+
+def test_graph_capture_replays_integrate_h(fgi, water):
+    prob, B, H, _ = water
+    ctx = fgi.Context(0).load(prob, "fp64")
+    v = dev(prob.v)
+    h = torch.empty(ctx.sizes()[1], dtype=torch.float64, device="cuda:0")
+    ws = ctx.workspace()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.integrate_h(v, h, ws=ws, stream=s)       # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.integrate_h(v, h, ws=ws, stream=s)
+    h.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(h.cpu().numpy(), stored(ctx, H), rtol=0, atol=1e-11 * np.abs(H).max())
+
+
+def test_nonfinite_potential_is_reported(fgi, water):
+    prob, _, _, _ = water
+    ctx = fgi.Context(0).load(prob, "fp64")
+    v = prob.v.copy()
+    v[17] = np.nan
+    ctx.integrate_h(dev(v))
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+    ctx.integrate_h(dev(prob.v))
+    ctx.sync()                                    # status word was cleared
+
+
+def test_workspace_errors(fgi, water):
+    prob, _, _, _ = water
+    ctx = fgi.Context(0).load(prob, "fp64")
+    v = dev(prob.v)
+    small = torch.empty(256, dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.integrate_h(v, ws=small)
+    assert e.value.code == -4
