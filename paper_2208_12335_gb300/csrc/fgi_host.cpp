@@ -371,10 +371,32 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         d.coef_off = (long long)(coef.size() / 4);
         d.nk = r.nk;
         d.l = r.l;
+        d.inv_h_hi = (float)d.inv_h;
+        d.inv_h_lo = (float)(d.inv_h - (double)d.inv_h_hi);
+        d.rcut_f = (float)d.rcut;
+        d.pad = 0;
         coef.insert(coef.end(), r.coef.begin(), r.coef.end());
         drad.push_back(d);
     }
-    std::vector<float> coef32(coef.begin(), coef.end());
+    // coefficients as double-floats: per interval (hi0..hi3), (lo0..lo3)
+    std::vector<float> coef_dd(coef.size() * 2);
+    for (size_t k = 0; k < coef.size() / 4; k++)
+        for (int q = 0; q < 4; q++) {
+            const float hi = (float)coef[4 * k + q];
+            coef_dd[8 * k + q] = hi;
+            coef_dd[8 * k + 4 + q] = (float)(coef[4 * k + q] - (double)hi);
+        }
+    auto to_dd = [](const std::vector<double> &xyz) {
+        std::vector<float> out(xyz.size() * 2);
+        for (size_t i = 0; i < xyz.size() / 3; i++)
+            for (int k = 0; k < 3; k++) {
+                const float hi = (float)xyz[3 * i + k];
+                out[6 * i + 2 * k] = hi;
+                out[6 * i + 2 * k + 1] = (float)(xyz[3 * i + k] - (double)hi);
+            }
+        return out;
+    };
+    std::vector<float> pts_dd = to_dd(c->pts), atom_dd = to_dd(c->atom_xyz);
     std::vector<DevSpecies> dsp;
     std::vector<int> shell_rad;
     for (const SpeciesH &s : c->species) {
@@ -420,7 +442,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_sp = add(dsp.data(), dsp.size() * sizeof(DevSpecies)),
            i_shr = add(shell_rad.data(), shell_rad.size() * 4),
            i_rad = add(drad.data(), drad.size() * sizeof(DevRadial)),
-           i_coef = add(coef.data(), coef.size() * 8), i_coef32 = add(coef32.data(), coef32.size() * 4),
+           i_coef = add(coef.data(), coef.size() * 8), i_coefdd = add(coef_dd.data(), coef_dd.size() * 4),
+           i_ptsdd = add(pts_dd.data(), pts_dd.size() * 4), i_atdd = add(atom_dd.data(), atom_dd.size() * 4),
            i_snat = add(sys_nat.data(), sys_nat.size() * 4),
            i_spo = add(c->sys_pair_off.data(), c->sys_pair_off.size() * 8),
            i_pp = add(c->pairpos.data(), c->pairpos.size() * 4),
@@ -454,7 +477,9 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     P.shell_rad = (const int *)at(i_shr);
     P.radials = (const DevRadial *)at(i_rad);
     P.coef = (const double *)at(i_coef);
-    P.coef32 = (const float *)at(i_coef32);
+    P.coef_dd = (const float4 *)at(i_coefdd);
+    P.pts_dd = (const float *)at(i_ptsdd);
+    P.atom_dd = (const float *)at(i_atdd);
     P.sys_nat = (const int *)at(i_snat);
     P.sys_pair_off = (const long long *)at(i_spo);
     P.pairpos = (const int *)at(i_pp);
@@ -813,9 +838,17 @@ int fgi_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void
         }
         return FGI_OK;
     }
-    std::string terr;
-    rc = tc_integrate_h(c->tc, c->dp, c->precision == FGI_SPLIT_BF16 ? 3 : 1, v, h, ws, s, &terr);
-    if (rc) return set_err(c, rc, "%s", terr.c_str());
+    const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+    DevPlan P = c->dp;
+    P.batches = c->d_batches_f64;
+    for (const TcWave &w : c->tc.waves) {
+        {
+            ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+            CUDA_TRY(c, tc_launch_phi(c->tc, P, w, v, ws, n_split, s));
+        }
+        ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
+        CUDA_TRY(c, tc_launch_h(c->tc, P, w, ws, h, n_split, s));
+    }
     return FGI_OK;
 }
 
@@ -842,9 +875,19 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
                                            nullptr, s));
         }
     } else {
-        std::string terr;
-        rc = tc_density(c->tc, c->dp, c->precision == FGI_SPLIT_BF16 ? 3 : 1, d, 1.0, n, ws, s, &terr);
-        if (rc) return set_err(c, rc, "%s", terr.c_str());
+        const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+        for (const TcWave &w : c->tc.waves) {
+            {
+                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+                CUDA_TRY(c, tc_launch_phi_cols(c->tc, P, w, ws, n_split, s));
+            }
+            {
+                ProfScope ps(c, s, 4, 0.0, w.g_bytes);
+                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, d, 1.0, ws, n_split, s));
+            }
+            ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
+            CUDA_TRY(c, tc_launch_density(c->tc, P, w, ws, n, n_split, s));
+        }
     }
     if (traces) {
         CUDA_TRY(c, cudaMemsetAsync(traces, 0, (size_t)c->n_sys * sizeof(double), s));

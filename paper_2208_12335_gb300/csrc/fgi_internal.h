@@ -20,6 +20,9 @@ struct DevRadial {
     double h, inv_h, rcut;
     long long coef_off;   // in units of 4 coefficients (one interval)
     int nk, l;
+    float inv_h_hi, inv_h_lo;   // 1/h as a double-float
+    float rcut_f;               // cutoff rounded to FP32
+    int pad;
 };
 
 struct DevSpecies {
@@ -64,7 +67,9 @@ struct DevPlan {
     const int *shell_rad;         // radial id per species shell
     const DevRadial *radials;
     const double *coef;           // [sum intervals][4] FP64
-    const float *coef32;          // the same in FP32
+    const float4 *coef_dd;        // [sum intervals][2]: the four coefficients as double-floats (hi, lo)
+    const float *pts_dd;          // [n_pts][6]: x, y, z as double-floats (xh, xl, yh, yl, zh, zl)
+    const float *atom_dd;         // [n_atoms][6]: the same for atom positions
     // systems
     const int *sys_nat;           // atoms per system
     const long long *sys_pair_off;// offset of the system's pairpos table

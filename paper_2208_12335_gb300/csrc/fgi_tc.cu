@@ -1,21 +1,1257 @@
-// Tensor-core path (placeholder until the tcgen05 kernels land).
-#include "fgi_tc.h"
+// Tensor-core path for sm_103a: basis evaluation into swizzled BF16 operand
+// images, the H contraction h_b = Phi_b^T diag(w v) Phi_b on tcgen05 with
+// FP64 atomic scatter, the D_b gather, and the density contraction
+// n_p = sum_j (D_b Phi_b^T)_jp phi_j(p) on tcgen05.
+//
+// Precision: every value x entering a contraction is split into three BF16
+// terms x = x0 + x1 + x2 (round to nearest at each step, so |x - sum| is
+// about 2^-24 |x|); the six products of combined order <= 2 are accumulated
+// in FP32 in tensor memory, x0*y0 in its own accumulator and the five
+// smaller ones in a second; the two are combined in FP64 and every
+// cross-batch sum is FP64.  n_split = 1 keeps x0*y0 only (plain BF16).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
 #include "../../include/fgi.h"
+#include "fgi_basis.cuh"
+#include "fgi_dd.cuh"
+#include "fgi_index.cuh"
+#include "fgi_tc.h"
 
 namespace fgi {
 
-int tc_build(TcPlan &t, const TcPlanInput &, std::string *) { t.built = false; t.ws_bytes = 0; return FGI_OK; }
-void tc_free(TcPlan &t) { t.built = false; }
-size_t tc_workspace_bytes(const TcPlan &t) { return t.ws_bytes; }
-int tc_integrate_h(TcPlan &, const DevPlan &, int, const double *, double *, void *, cudaStream_t, std::string *err)
+namespace {
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    *err = "tensor-core path not available";
-    return FGI_ERR_UNSUPPORTED;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-int tc_density(TcPlan &, const DevPlan &, int, const double *, double, double *, void *, cudaStream_t, std::string *err)
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    *err = "tensor-core path not available";
-    return FGI_ERR_UNSUPPORTED;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a wait that long means a bug
+
+// Bounded wait on an mbarrier phase; on time-out records kStatusTimeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread (lane) gets its row's 32 values
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, 128-byte swizzle (tcgen05 format: version 1).
+// K-major: rows of 64 BF16 (128 B), 8-row atoms of 1 KB; sbo = atom stride.
+// MN-major: lbo = stride between 64-element MN atoms, sbo = stride between
+// 8-row K groups.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> F32, dense.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// --------------------------------------------------------------- splitting
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// x = x0 + x1 + x2 with each term BF16, rounded to nearest in turn.
+__device__ __forceinline__ void split3(double x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    a = __double2bfloat16(x);
+    double r = x - (double)__bfloat162float(a);
+    b = __double2bfloat16(r);
+    r -= (double)__bfloat162float(b);
+    c = __double2bfloat16(r);
+}
+
+__device__ __forceinline__ void store_split8d(uint8_t *dst, long long plane, const double *x, int n_split)
+{
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split3(x[2 * q], a0, a1, a2);
+        split3(x[2 * q + 1], b0, b1, b2);
+        w0[q] = pack_bf16(a0, b0);
+        w1[q] = pack_bf16(a1, b1);
+        w2[q] = pack_bf16(a2, b2);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    if (n_split > 1) *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    if (n_split > 2) *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// byte offset of the 16-byte unit (row r, 8-column group g) inside chunk (blk, c)
+__device__ __forceinline__ long long unit_offset(int blk, int nchunk, int c, int r, int g)
+{
+    return ((long long)(blk * nchunk + c) * 16 + (r >> 3)) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4);
+}
+
+// Normalisation constants of the real spherical harmonics as double-floats.
+#define FGI_DF_CONST(c) {(float)(c), (float)((c) - (double)(float)(c))}
+__constant__ float2 kYlmC[10] = {
+    FGI_DF_CONST(0.28209479177387814),  // l0
+    FGI_DF_CONST(0.4886025119029199),   // l1
+    FGI_DF_CONST(1.0925484305920792),   // l2: xy, yz, xz
+    FGI_DF_CONST(0.31539156525252005),  // l2: 2z^2 - x^2 - y^2
+    FGI_DF_CONST(0.5462742152960396),   // l2: x^2 - y^2
+    FGI_DF_CONST(0.5900435899266435),   // l3: y(3x^2 - y^2), x(x^2 - 3y^2)
+    FGI_DF_CONST(2.890611442640554),    // l3: xyz
+    FGI_DF_CONST(0.4570457994644658),   // l3: y(4z^2 - x^2 - y^2), x(...)
+    FGI_DF_CONST(0.3731763325901154),   // l3: z(2z^2 - 3x^2 - 3y^2)
+    FGI_DF_CONST(1.445305721320277)};   // l3: z(x^2 - y^2)
+#undef FGI_DF_CONST
+
+// r^l Y_lm = C_lm * Q_lm(x, y, z): Q with small integer coefficients (FP32),
+// the constant index into kYlmC.
+__device__ __forceinline__ void ylm_poly_f32(int l, float x, float y, float z, float *Q, int *ci)
+{
+    if (l == 0) {
+        Q[0] = 1.f; ci[0] = 0;
+    } else if (l == 1) {
+        Q[0] = y; Q[1] = z; Q[2] = x;
+        ci[0] = ci[1] = ci[2] = 1;
+    } else if (l == 2) {
+        Q[0] = x * y; Q[1] = y * z; Q[2] = 2.f * z * z - x * x - y * y; Q[3] = x * z; Q[4] = x * x - y * y;
+        ci[0] = 2; ci[1] = 2; ci[2] = 3; ci[3] = 2; ci[4] = 4;
+    } else {
+        const float q = 4.f * z * z - x * x - y * y;
+        Q[0] = y * (3.f * x * x - y * y); Q[1] = x * y * z; Q[2] = y * q;
+        Q[3] = z * (2.f * z * z - 3.f * x * x - 3.f * y * y); Q[4] = x * q; Q[5] = z * (x * x - y * y);
+        Q[6] = x * (x * x - 3.f * y * y);
+        ci[0] = 5; ci[1] = 6; ci[2] = 7; ci[3] = 8; ci[4] = 7; ci[5] = 9; ci[6] = 5;
+    }
+}
+
+// 3-term BF16 split of a double-float value
+__device__ __forceinline__ void split3_df(df x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    a = __float2bfloat16_rn(x.hi);
+    float r = (x.hi - __bfloat162float(a)) + x.lo;
+    b = __float2bfloat16_rn(r);
+    r -= __bfloat162float(b);
+    c = __float2bfloat16_rn(r);
+}
+
+__device__ __forceinline__ void store_split8_df(uint8_t *dst, long long plane, const df *x, int n_split)
+{
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split3_df(x[2 * q], a0, a1, a2);
+        split3_df(x[2 * q + 1], b0, b1, b2);
+        w0[q] = pack_bf16(a0, b0);
+        w1[q] = pack_bf16(a1, b1);
+        w2[q] = pack_bf16(a2, b2);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    if (n_split > 1) *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    if (n_split > 2) *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// Split with a fixed-point leading term: x0 = m * unit, m = rint(x / unit),
+// unit = 2^(e-7) with 2^e >= the row's largest |x|, so |m| <= 128 and every
+// product x0*y0 of a row pair is an integer multiple of unit_x*unit_y not
+// exceeding 2^14 in units; a sum of up to 1024 of them (a batch) is exact in
+// FP32 whatever the accumulator's rounding.  The remainder x - x0 is split
+// relative to itself into two BF16 terms.
+__device__ __forceinline__ void split_fixed(df x, float scale, float unit, __nv_bfloat16 &a,
+                                            __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    const float x0 = rintf(x.hi * scale) * unit;
+    const df r = df_two_sum(x.hi - x0, x.lo);
+    a = __float2bfloat16_rn(x0);
+    b = __float2bfloat16_rn(r.hi);
+    c = __float2bfloat16_rn((r.hi - __bfloat162float(b)) + r.lo);
+}
+
+__device__ __forceinline__ void store_fixed8v(uint8_t *dst, long long plane, const df *x, const float *scale,
+                                              const float *unit)
+{
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split_fixed(x[2 * q], scale[2 * q], unit[2 * q], a0, a1, a2);
+        split_fixed(x[2 * q + 1], scale[2 * q + 1], unit[2 * q + 1], b0, b1, b2);
+        w0[q] = pack_bf16(a0, b0);
+        w1[q] = pack_bf16(a1, b1);
+        w2[q] = pack_bf16(a2, b2);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+__device__ __forceinline__ void store_fixed8(uint8_t *dst, long long plane, const df *x, float scale, float unit)
+{
+    uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split_fixed(x[2 * q], scale, unit, a0, a1, a2);
+        split_fixed(x[2 * q + 1], scale, unit, b0, b1, b2);
+        w0[q] = pack_bf16(a0, b0);
+        w1[q] = pack_bf16(a1, b1);
+        w2[q] = pack_bf16(a2, b2);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// Power-of-two scale 2^(b-e) and unit 2^(e-b) for a row whose largest |x|
+// is mx: |x| * scale <= 2^b.  b digit bits keep the exact sum: 2^(2b) times
+// the contraction depth must not exceed 2^24.  Rows below 1e-30 (negligible
+// against any stored value) put everything in the remainder terms.
+__device__ __forceinline__ int fixed_bits(int depth)
+{
+    int b = 7;
+    while (b > 1 && ((long long)depth << (2 * b)) > (1ll << 24)) b--;
+    return b;
+}
+
+__device__ __forceinline__ void fixed_scale(float mx, int bits, float &scale, float &unit)
+{
+    if (!(mx > 1e-30f)) {
+        scale = 0.f;
+        unit = 0.f;
+        return;
+    }
+    int e;
+    frexpf(mx * (1.f + 1.f / 4096.f), &e);
+    scale = ldexpf(1.f, bits - e);
+    unit = ldexpf(1.f, e - bits);
+}
+
+// FP32 phi of one atom's functions at one point (first pass of the H images:
+// only the row maxima are taken from it)
+__device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const float4 *coef_dd, float d)
+{
+    if (d >= R.rcut_f) return 0.f;
+    if (d < 1e-12f) return R.l == 0 ? __ldg(coef_dd + 2 * R.coef_off).y * R.inv_h_hi : 0.f;
+    const float s = d * R.inv_h_hi;
+    int k = (int)s;
+    if (k > R.nk - 2) k = R.nk - 2;
+    const float t = s - (float)k;
+    const float4 c = __ldg(coef_dd + 2 * (R.coef_off + k));
+    float u = c.x + t * (c.y + t * (c.z + t * c.w));
+    float r = u / d;
+    for (int q = 0; q < R.l; q++) r /= d;
+    return r;
+}
+
+constexpr int kPhiValStride = 65;   // float2 per row of phi_smem (padding against bank conflicts)
+
+// Double-float phi for rows [r0, r0+128) (atoms e0..e0+ne-1 of the batch)
+// at the 64 points of chunk c, into phi_smem[row - r0][point] (zero for
+// points beyond the batch).
+__device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatch &B, const DevAct *act, int e0,
+                                                 int ne, int r0, int c, float2 *phi_smem)
+{
+    for (int u = threadIdx.x; u < ne * 64; u += blockDim.x) {
+        const int e = e0 + (u >> 6), k = u & 63, p = c * 64 + k;
+        const DevAct A = act[e];
+        const DevSpecies S = P.species[P.atom_species[A.atom]];
+        const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
+        float2 *out = phi_smem + (A.fn_loc - r0) * kPhiValStride + k;
+        if (p >= B.np) {
+            for (int f = f_lo; f < f_hi; f++) out[f * kPhiValStride] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+        const float *aa = P.atom_dd + 6 * A.atom;
+        const df x = df_sub(df{pp[0], pp[1]}, df{aa[0], aa[1]});
+        const df y = df_sub(df{pp[2], pp[3]}, df{aa[2], aa[3]});
+        const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
+        const df d = df_sqrt(df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z)));
+        const bool origin = d.hi < 1e-12f;
+        const df inv = origin ? df{0.f, 0.f} : df_rcp(d);
+        int f = 0;
+        for (int sh = 0; sh < S.n_shell; sh++) {
+            const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+            const int nm = 2 * R.l + 1;
+            if (f + nm <= f_lo || f >= f_hi) {
+                f += nm;
+                continue;
+            }
+            df rad{0.f, 0.f};                      // u(d)/d^(l+1)
+            if (d.hi < R.rcut_f) {
+                if (origin) {
+                    if (R.l == 0) {
+                        const float4 ch = __ldg(P.coef_dd + 2 * R.coef_off), cl = __ldg(P.coef_dd + 2 * R.coef_off + 1);
+                        rad = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});
+                    }
+                } else {
+                    const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
+                    int kk = (int)floorf(s.hi);
+                    kk = max(0, min(kk, R.nk - 2));
+                    const df t = df_two_sum(s.hi - (float)kk, s.lo);
+                    const float4 ch = __ldg(P.coef_dd + 2 * (R.coef_off + kk));
+                    const float4 cl = __ldg(P.coef_dd + 2 * (R.coef_off + kk) + 1);
+                    df uu{ch.w, cl.w};
+                    uu = df_add(df_mul(uu, t), df{ch.z, cl.z});
+                    uu = df_add(df_mul(uu, t), df{ch.y, cl.y});
+                    uu = df_add(df_mul(uu, t), df{ch.x, cl.x});
+                    rad = df_mul(uu, inv);
+                    for (int q = 0; q < R.l; q++) rad = df_mul(rad, inv);
+                }
+            }
+            float Q[7];
+            int ci[7];
+            ylm_poly_f32(R.l, x.hi, y.hi, z.hi, Q, ci);
+            for (int m = 0; m < nm; m++, f++) {
+                if (f < f_lo || f >= f_hi) continue;
+                const float2 cc = kYlmC[ci[m]];
+                const df val = df_mul_f(df_mul(rad, df{cc.x, cc.y}), Q[m]);
+                out[f * kPhiValStride] = make_float2(val.hi, val.lo);
+            }
+        }
+    }
+}
+
+// -------------------------------------------- basis -> operand images (K1)
+// CTA per (batch, 128-row block).  For each 64-point chunk: evaluate phi for
+// the block's rows into shared memory, then write the split planes of phi
+// (and of w v phi when v is given) as swizzled 16-byte units.
+//
+// The radial factor N_lm u(d)/d^(l+1) -- shared by all angular points of a
+// radial shell, so its rounding would be systematic -- is evaluated in
+// double-float from a double-float spline table and double-float
+// coordinates; only the angular polynomial Q_lm(x, y, z) is FP32 (its
+// rounding varies from point to point).
+
+__global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                uint8_t *ws, const double *v, int n_split, int fixed)
+{
+    extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
+    __shared__ float2 wv[64];
+    __shared__ unsigned int rowmax[2][128];          // |phi|, |w v phi| maxima (float bits)
+    __shared__ float fsc[2][128][2];                 // per row: scale, unit
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int I = it.ti;
+    const int r0 = I * 128;
+    const DevAct *act = P.act + B.act0;
+    const int rend = min(r0 + 128, B.nfn);
+    const int e0 = find_act(act, B.n_act, r0);
+    const int e1 = find_act(act, B.n_act, rend - 1);
+    const int ne = e1 - e0 + 1;
+    uint8_t *phi_img = ws + T.img_phi;
+    uint8_t *a_img = ws + T.img_aux;
+    if (fixed) {
+        // pass 1: row maxima of |phi| and |w v phi| over the batch's points (FP32)
+        for (int q = threadIdx.x; q < 256; q += blockDim.x) (&rowmax[0][0])[q] = 0u;
+        __syncthreads();
+        const int units = ne * 64 * T.nc;
+        for (int u0 = 0; u0 < units; u0 += blockDim.x) {
+            const int u = u0 + threadIdx.x;
+            const bool in = u < units;
+            const int uu = in ? u : 0;
+            const int e = e0 + (uu >> 6) % ne, c = (uu >> 6) / ne, k = uu & 63, p = c * 64 + k;
+            const DevAct A = act[e];
+            const DevSpecies S = P.species[P.atom_species[A.atom]];
+            const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
+            const bool live = in && p < B.np;
+            float x = 0.f, y = 0.f, z = 0.f, wvp = 0.f;
+            if (live) {
+                const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                const float *aa = P.atom_dd + 6 * A.atom;
+                x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+                y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+                z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+                wvp = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p]));
+            }
+            const float d = sqrtf(x * x + y * y + z * z);
+            int f = 0;
+            for (int sh = 0; sh < S.n_shell; sh++) {
+                const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                const int nm = 2 * R.l + 1;
+                if (f + nm <= f_lo || f >= f_hi) {
+                    f += nm;
+                    continue;
+                }
+                const float rad = live ? radial_over_d_f32(R, P.coef_dd, d) : 0.f;
+                float Q[7];
+                int ci[7];
+                ylm_poly_f32(R.l, x, y, z, Q, ci);
+                for (int m = 0; m < nm; m++, f++) {
+                    float a = fabsf(rad * kYlmC[ci[m]].x * Q[m]);
+                    if (!(a < 3.0e38f)) a = 3.0e38f;           // non-finite input: keep the scale finite
+                    unsigned int mp = __float_as_uint(a), ma = __float_as_uint(fminf(a * wvp, 3.0e38f));
+                    // a warp holds 32 consecutive points of one atom and chunk
+                    mp = __reduce_max_sync(0xffffffffu, mp);
+                    ma = __reduce_max_sync(0xffffffffu, ma);
+                    if ((threadIdx.x & 31) == 0 && f >= f_lo && f < f_hi) {
+                        atomicMax(&rowmax[0][A.fn_loc + f - r0], mp);
+                        atomicMax(&rowmax[1][A.fn_loc + f - r0], ma);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int which = threadIdx.x >> 7, r = threadIdx.x & 127;
+            float sc, un;
+            fixed_scale(__uint_as_float(rowmax[which][r]), fixed_bits(T.nc * 64), sc, un);
+            fsc[which][r][0] = sc;
+            fsc[which][r][1] = un;
+        }
+        __syncthreads();
+    }
+    for (int c = 0; c < T.nc_alloc; c++) {
+        eval_block_chunk(P, B, act, e0, ne, r0, c, phi_smem);
+        if (threadIdx.x < 64) {
+            const int p = c * 64 + threadIdx.x;
+            double s = 0.0;
+            if (v && p < B.np) {
+                const double vv = v[B.pt0 + p];
+                if (!isfinite(vv)) atomicOr(P.status, kStatusNonFinite);
+                s = P.pw[B.pt0 + p] * vv;
+            }
+            const df sd = df_from_double(s);
+            wv[threadIdx.x] = make_float2(sd.hi, sd.lo);
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+            const int r = u >> 3, g = u & 7;
+            const bool live = r0 + r < B.nfn;
+            df x[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float2 t = live ? phi_smem[r * kPhiValStride + g * 8 + q] : make_float2(0.f, 0.f);
+                x[q] = df{t.x, t.y};
+            }
+            const long long off = unit_offset(I, T.nc_alloc, c, r, g);
+            if (fixed)
+                store_fixed8(phi_img + off, T.plane_phi, x, fsc[0][r][0], fsc[0][r][1]);
+            else
+                store_split8_df(phi_img + off, T.plane_phi, x, n_split);
+            if (v) {
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const float2 s = wv[g * 8 + q];
+                    x[q] = df_mul(x[q], df{s.x, s.y});
+                }
+                if (fixed)
+                    store_fixed8(a_img + off, T.plane_phi, x, fsc[1][r][0], fsc[1][r][1]);
+                else
+                    store_split8_df(a_img + off, T.plane_phi, x, n_split);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// CTA per (batch, 64-point chunk c): the phi image for the density.  The
+// density contracts over functions, so the fixed-point grid of the leading
+// term is per point (column): first the largest |phi_i(p)| over all of the
+// batch's functions (FP32), then every 128-row block in double-float.
+__global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                     uint8_t *ws, int n_split)
+{
+    extern __shared__ float2 phi_smem[];
+    __shared__ unsigned int colmax[64];
+    __shared__ float csc[2][64];
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int c = it.ti;
+    const DevAct *act = P.act + B.act0;
+    uint8_t *phi_img = ws + T.img_phi;
+    const bool fixed = n_split == 3;
+    if (fixed) {
+        if (threadIdx.x < 64) colmax[threadIdx.x] = 0u;
+        __syncthreads();
+        for (int u = threadIdx.x; u < B.n_act * 64; u += blockDim.x) {
+            const int e = u >> 6, k = u & 63, p = c * 64 + k;
+            if (p >= B.np) continue;
+            const DevAct A = act[e];
+            const DevSpecies S = P.species[P.atom_species[A.atom]];
+            const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+            const float *aa = P.atom_dd + 6 * A.atom;
+            const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+            const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+            const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+            const float d = sqrtf(x * x + y * y + z * z);
+            float mx = 0.f;
+            for (int sh = 0; sh < S.n_shell; sh++) {
+                const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                const float rad = radial_over_d_f32(R, P.coef_dd, d);
+                float Q[7];
+                int ci[7];
+                ylm_poly_f32(R.l, x, y, z, Q, ci);
+                for (int m = 0; m < 2 * R.l + 1; m++) mx = fmaxf(mx, fabsf(rad * kYlmC[ci[m]].x * Q[m]));
+            }
+            if (!(mx < 3.0e38f)) mx = 3.0e38f;
+            atomicMax(&colmax[k], __float_as_uint(mx));
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            float sc, un;
+            fixed_scale(__uint_as_float(colmax[threadIdx.x]), fixed_bits(T.nkc * 64), sc, un);
+            csc[0][threadIdx.x] = sc;
+            csc[1][threadIdx.x] = un;
+        }
+        __syncthreads();
+    }
+    for (int I = 0; I < T.nrb; I++) {
+        const int r0 = I * 128;
+        const int rend = min(r0 + 128, B.nfn);
+        const int e0 = find_act(act, B.n_act, r0);
+        const int e1 = find_act(act, B.n_act, rend - 1);
+        eval_block_chunk(P, B, act, e0, e1 - e0 + 1, r0, c, phi_smem);
+        __syncthreads();
+        for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+            const int r = u >> 3, g = u & 7;
+            const bool live = r0 + r < B.nfn;
+            df x[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float2 t = live ? phi_smem[r * kPhiValStride + g * 8 + q] : make_float2(0.f, 0.f);
+                x[q] = df{t.x, t.y};
+            }
+            const long long off = unit_offset(I, T.nc_alloc, c, r, g);
+            if (fixed)
+                store_fixed8v(phi_img + off, T.plane_phi, x, &csc[0][g * 8], &csc[1][g * 8]);
+            else
+                store_split8_df(phi_img + off, T.plane_phi, x, n_split);
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------- H contraction on tcgen05 (K2)
+// CTA per tile (batch, I, J), I <= J: 128 x 128 outputs, K = points in
+// chunks of 64.  Warp 4: bulk-copy producer; warp 5: MMA issuer; warps 0-3:
+// epilogue (TMEM lanes 32w..32w+31), FP64 atomic scatter of the upper triangle.
+constexpr int kThreadsTc = 192;
+
+struct TcSmem {
+    uint64_t full, empty, done, acc_empty;
+    uint32_t tmem;
+    int pad[7];
+    FnRef ref[128];
+};
+
+__global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                        const uint8_t *ws, double *h, int n_split)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *a_sm = sm;
+    uint8_t *b_sm = sm + n_split * kChunkBytes;
+    TcSmem *S = reinterpret_cast<TcSmem *>(sm + 2 * n_split * kChunkBytes);
+
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const DevAct *act = P.act + B.act0;
+    const int i0 = it.ti * 128, j0 = it.tj * 128;
+    if (threadIdx.x < 128 && j0 + (int)threadIdx.x < B.nfn) {
+        const int j = j0 + threadIdx.x;
+        S->ref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, j), j);
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&S->full, 1);
+        mbar_init(&S->empty, 1);
+        mbar_init(&S->done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        tmem_alloc(&S->tmem, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem;
+    const uint32_t chunk = (uint32_t)n_split * kChunkBytes;
+    const uint8_t *a_img = ws + T.img_aux;
+    const uint8_t *b_img = ws + T.img_phi;
+    const int nc = T.nc;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (int c = 0; c < nc; c++) {
+                if (c > 0 && !mbar_wait(&S->empty, (c - 1) & 1, P.status)) break;
+                mbar_expect_tx(&S->full, 2 * chunk);
+                for (int s = 0; s < n_split; s++) {
+                    bulk_g2s(a_sm + s * kChunkBytes,
+                             a_img + s * T.plane_phi + (long long)(it.ti * T.nc_alloc + c) * kChunkBytes,
+                             kChunkBytes, &S->full);
+                    bulk_g2s(b_sm + s * kChunkBytes,
+                             b_img + s * T.plane_phi + (long long)(it.tj * T.nc_alloc + c) * kChunkBytes,
+                             kChunkBytes, &S->full);
+                }
+            }
+            // do not leave while a copy may still be landing
+            mbar_wait(&S->empty, (nc - 1) & 1, P.status);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, 128, false, false);
+            bool started[2] = {false, false};
+            bool ok = true;
+            for (int c = 0; c < nc && ok; c++) {
+                if (!mbar_wait(&S->full, c & 1, P.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++) {
+                    for (int pa = 0; pa < n_split; pa++) {
+                        for (int pb = 0; pb < n_split; pb++) {
+                            // split: every product but x2*y2 (x0*y0 alone in accumulator 0)
+                            if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
+                            const int acc = (pa + pb == 0) ? 0 : 1;
+                            const uint64_t ad = desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
+                            const uint64_t bd = desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 32), 16, 1024);
+                            tc_mma(tmem + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
+                            started[acc] = true;
+                        }
+                    }
+                }
+                tc_commit(&S->empty);
+            }
+            tc_commit(&S->done);
+        }
+    }
+    __syncwarp();
+
+    if (warp < 4) {
+        const bool ok = mbar_wait(&S->done, 0, P.status);
+        tc_fence_after();
+        const int r = warp * 32 + lane;
+        const int i = i0 + r;
+        const bool row_ok = ok && i < B.nfn;
+        FnRef rref{};
+        if (row_ok) rref = fn_ref(P, act, find_act(act, B.n_act, i), i);
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int cc = 0; cc < 4; cc++) {
+            if (j0 + cc * 32 >= B.nfn) break;
+            float a0[32], a1[32];
+            tmem_ld32(tmem + lane_base + cc * 32, a0);
+            if (n_split > 1) tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
+            tmem_wait_ld();
+            if (!row_ok) continue;
+#pragma unroll
+            for (int q = 0; q < 32; q++) {
+                const int jl = cc * 32 + q;
+                const int j = j0 + jl;
+                if (j >= B.nfn || i > j) continue;
+                const double val = (double)a0[q] + (n_split > 1 ? (double)a1[q] : 0.0);
+                const long long k = value_index(P, B.sys, rref, S->ref[jl]);
+                if (k >= 0) atomicAdd(h + k, val);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------- D_b gather (K3a)
+// CTA per (batch, 128-row block J): D(j, i) for local functions j (rows) and
+// i (columns) from the stored upper triangle, split into BF16 planes as a
+// K-major swizzled image.  In the split mode the leading term is fixed-point
+// on a per-row grid (the density contracts over i), found by a first pass
+// over the row block.
+__device__ __forceinline__ double gather_d_value(const DevPlan &P, const DevBatch &B, const FnRef &rj,
+                                                 const FnRef &ci, int j, int i, const double *dval,
+                                                 double offdiag_scale)
+{
+    if (j >= B.nfn || i >= B.nfn) return 0.0;
+    const FnRef &a = (i <= j) ? ci : rj;
+    const FnRef &b = (i <= j) ? rj : ci;
+    const long long k = value_index(P, B.sys, a, b);
+    return k >= 0 ? __ldg(dval + k) * (i == j ? 1.0 : offdiag_scale) : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                     uint8_t *ws, const double *dval, double offdiag_scale,
+                                                     int n_split)
+{
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int J = it.ti;
+    __shared__ FnRef rref[128], cref[64];
+    __shared__ unsigned int rowmax[128];
+    __shared__ float rsc[2][128];
+    const DevAct *act = P.act + B.act0;
+    const bool fixed = n_split == 3;
+    if (threadIdx.x < 128) {
+        const int j = J * 128 + threadIdx.x;
+        if (j < B.nfn) rref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, j), j);
+        rowmax[threadIdx.x] = 0u;
+    }
+    uint8_t *img = ws + T.img_aux;
+    for (int pass = fixed ? 0 : 1; pass < 2; pass++) {
+        if (pass == 1 && fixed) {
+            __syncthreads();
+            if (threadIdx.x < 128) {
+                float sc, un;
+                fixed_scale(__uint_as_float(rowmax[threadIdx.x]), fixed_bits(T.nkc * 64), sc, un);
+                rsc[0][threadIdx.x] = sc;
+                rsc[1][threadIdx.x] = un;
+            }
+        }
+        for (int kc = 0; kc < T.nkc; kc++) {
+            __syncthreads();
+            if (threadIdx.x < 64) {
+                const int i = kc * 64 + threadIdx.x;
+                if (i < B.nfn) cref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, i), i);
+            }
+            __syncthreads();
+            for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+                const int r = u >> 3, g = u & 7;
+                const int j = J * 128 + r;
+                double x[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int il = g * 8 + q;
+                    x[q] = gather_d_value(P, B, rref[r], cref[il], j, kc * 64 + il, dval, offdiag_scale);
+                }
+                if (pass == 0) {
+                    float mx = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) mx = fmaxf(mx, fabsf((float)x[q]));
+                    if (!(mx < 3.0e38f)) mx = 3.0e38f;
+                    atomicMax(&rowmax[r], __float_as_uint(mx));
+                    continue;
+                }
+                uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
+                if (fixed) {
+                    df xd[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) xd[q] = df_from_double(x[q]);
+                    store_fixed8(dst, T.plane_d, xd, rsc[0][r], rsc[1][r]);
+                } else {
+                    store_split8d(dst, T.plane_d, x, n_split);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- density on tcgen05 (K3b)
+// CTA per (batch, 128-point tile m).  For each 128-function block J:
+// E^T[j][p] = sum_i D[j][i] phi_i(p) (A = D image, K-major; B = phi image
+// read as MN-major), then n_p += sum_j E^T[j][p] phi_j(p) in FP64: lane j
+// multiplies by its own phi row and the warp reduces over j.
+__global__ void __launch_bounds__(kThreadsTc, 2) k_tc_density(DevPlan P, const TcBatch *tb,
+                                                              const WorkItem *items, const uint8_t *ws,
+                                                              double *n_out, int n_split)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *a_sm = sm;                              // D chunk: n_split x 16 KB
+    uint8_t *b_sm = sm + n_split * kChunkBytes;      // phi chunk: n_split x (2 x 8 KB)
+    TcSmem *S = reinterpret_cast<TcSmem *>(sm + 2 * n_split * kChunkBytes);
+    __shared__ double red[4][128];
+
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int m = it.ti;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) (&red[0][0])[k] = 0.0;
+    if (threadIdx.x == 0) {
+        mbar_init(&S->full, 1);
+        mbar_init(&S->empty, 1);
+        mbar_init(&S->done, 1);
+        mbar_init(&S->acc_empty, 128);
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        tmem_alloc(&S->tmem, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem;
+    const uint32_t chunk = (uint32_t)n_split * kChunkBytes;
+    const uint8_t *d_img = ws + T.img_aux;
+    const uint8_t *phi_img = ws + T.img_phi;
+    const int nkc = T.nkc, nrb = T.nrb;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int n = 0;
+            bool ok = true;
+            for (int J = 0; J < nrb && ok; J++) {
+                for (int kc = 0; kc < nkc; kc++, n++) {
+                    if (n > 0 && !mbar_wait(&S->empty, (n - 1) & 1, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&S->full, 2 * chunk);
+                    const int I = kc >> 1, half = kc & 1;
+                    for (int s = 0; s < n_split; s++) {
+                        bulk_g2s(a_sm + s * kChunkBytes,
+                                 d_img + s * T.plane_d + (long long)(J * nkc + kc) * kChunkBytes, kChunkBytes,
+                                 &S->full);
+                        for (int c2 = 0; c2 < 2; c2++)
+                            bulk_g2s(b_sm + s * kChunkBytes + c2 * 8192,
+                                     phi_img + s * T.plane_phi +
+                                         ((long long)(I * T.nc_alloc + 2 * m + c2) * 16 + 8 * half) * 1024,
+                                     8192, &S->full);
+                    }
+                }
+            }
+            if (ok && n > 0) mbar_wait(&S->empty, (n - 1) & 1, P.status);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, 128, false, true);
+            int n = 0;
+            bool ok = true;
+            for (int J = 0; J < nrb && ok; J++) {
+                if (J > 0 && !mbar_wait(&S->acc_empty, (J - 1) & 1, P.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                bool started[2] = {false, false};
+                for (int kc = 0; kc < nkc; kc++, n++) {
+                    if (!mbar_wait(&S->full, n & 1, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int ks = 0; ks < 4; ks++) {
+                        for (int pa = 0; pa < n_split; pa++) {
+                            for (int pb = 0; pb < n_split; pb++) {
+                                if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
+                                const int acc = (pa + pb == 0) ? 0 : 1;
+                                const uint64_t ad =
+                                    desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
+                                const uint64_t bd =
+                                    desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 2048), 8192, 1024);
+                                tc_mma(tmem + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
+                                started[acc] = true;
+                            }
+                        }
+                    }
+                    tc_commit(&S->empty);
+                }
+                tc_commit(&S->done);     // accumulator of block J complete
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps 0-3: row j = J*128 + 32*warp + lane
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int J = 0; J < nrb; J++) {
+            const bool ok = mbar_wait(&S->done, J & 1, P.status);
+            tc_fence_after();
+            const int r = warp * 32 + lane;
+            const int j = J * 128 + r;
+            for (int cc = 0; cc < 4; cc++) {
+                float a0[32], a1[32];
+                tmem_ld32(tmem + lane_base + cc * 32, a0);
+                if (n_split > 1) tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
+                tmem_wait_ld();
+                if (cc == 3) {
+                    tc_fence_before();
+                    mbar_arrive(&S->acc_empty);   // accumulator may be overwritten
+                }
+                // phi_j(p) for the 32 points of this column chunk
+                const int c = 2 * m + (cc >> 1);
+                double prod[32];
+#pragma unroll
+                for (int gg = 0; gg < 4; gg++) {
+                    const int g = (cc & 1) * 4 + gg;
+                    const long long off = unit_offset(J, T.nc_alloc, c, r, g);
+                    float ph[8];
+                    {
+                        const uint4 u0 = *reinterpret_cast<const uint4 *>(phi_img + off);
+                        const uint32_t w0[4] = {u0.x, u0.y, u0.z, u0.w};
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            ph[2 * q] = __uint_as_float(w0[q] << 16);
+                            ph[2 * q + 1] = __uint_as_float(w0[q] & 0xFFFF0000u);
+                        }
+                    }
+                    double phd[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) phd[q] = (double)ph[q];
+                    for (int s = 1; s < n_split; s++) {
+                        const uint4 u1 = *reinterpret_cast<const uint4 *>(phi_img + off + s * T.plane_phi);
+                        const uint32_t w1[4] = {u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            phd[2 * q] += (double)__uint_as_float(w1[q] << 16);
+                            phd[2 * q + 1] += (double)__uint_as_float(w1[q] & 0xFFFF0000u);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int col = gg * 8 + q;
+                        const double e = (double)a0[col] + (n_split > 1 ? (double)a1[col] : 0.0);
+                        prod[col] = (ok && j < B.nfn) ? e * phd[q] : 0.0;
+                    }
+                }
+                // reduce over the 32 lanes (rows j): lane q ends with column q
+#pragma unroll
+                for (int w = 16; w >= 1; w >>= 1) {
+                    const bool upper = (lane & w) != 0;
+#pragma unroll
+                    for (int q = 0; q < w; q++) {
+                        const double send = upper ? prod[q] : prod[q + w];
+                        const double keep = upper ? prod[q + w] : prod[q];
+                        prod[q] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                    }
+                }
+                red[warp][cc * 32 + lane] += prod[0];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int p = m * 128 + threadIdx.x;
+        if (p < B.np)
+            n_out[B.pt0 + p] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    }
+    if (warp == 5) tmem_dealloc(tmem, 256);
+}
+
+// Dynamic shared memory of the tcgen05 kernels.  Launches always use the
+// 3-plane size so that at most two CTAs share an SM: each holds 256 of the
+// SM's 512 tensor-memory columns.
+size_t smem_tc(int n_split) { return 1024 + 2 * (size_t)n_split * kChunkBytes + sizeof(TcSmem); }
+
+size_t smem_phi() { return 128 * kPhiValStride * sizeof(float2); }
+
+bool attrs_set = false;
+
+cudaError_t set_attrs()
+{
+    if (attrs_set) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_phi_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi());
+    if (e != cudaSuccess) return e;
+    attrs_set = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ==================================================================== host
+int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
+{
+    tc_free(t);
+    t.batches.assign(in.n_batch, TcBatch{});
+    t.items.clear();
+    t.waves.clear();
+    size_t cap = (size_t)64 << 20;
+    if (const char *e = getenv("FGI_TC_WAVE_MB")) cap = (size_t)std::max(1L, atol(e)) << 20;
+    t.wave_cap = cap;
+    // per-batch image geometry and footprint (3 planes always reserved)
+    std::vector<size_t> foot(in.n_batch, 0);
+    for (int b = 0; b < in.n_batch; b++) {
+        const DevBatch &B = in.batches[b];
+        TcBatch &T = t.batches[b];
+        T.nrb = (B.nfn + 127) / 128;
+        T.nc = (B.np + 63) / 64;
+        T.nc_alloc = (T.nc + 1) / 2 * 2;
+        T.nkc = (B.nfn + 63) / 64;
+        T.plane_phi = (long long)T.nrb * T.nc_alloc * kChunkBytes;
+        T.plane_d = (long long)T.nrb * T.nkc * kChunkBytes;
+        foot[b] = 3 * (size_t)T.plane_phi + 3 * (size_t)std::max(T.plane_phi, T.plane_d);
+    }
+    size_t max_ws = 0;
+    TcWave w;
+    size_t off = 0;
+    auto close_wave = [&](int b_end) {
+        w.nb = b_end - w.b0;
+        if (w.nb <= 0) return;
+        max_ws = std::max(max_ws, off);
+        t.waves.push_back(w);
+    };
+    for (int b = 0; b < in.n_batch; b++) {
+        if (b > w.b0 && off + foot[b] > cap) {
+            close_wave(b);
+            w = TcWave{};
+            w.b0 = b;
+            off = 0;
+        }
+        TcBatch &T = t.batches[b];
+        T.img_phi = (long long)off;
+        T.img_aux = (long long)(off + 3 * (size_t)T.plane_phi);
+        off += foot[b];
+    }
+    close_wave(in.n_batch);
+    for (TcWave &wv : t.waves) {
+        auto live = [&](int b) { return in.batches[b].np > 0 && in.batches[b].nfn > 0; };
+        wv.phi0 = (long long)t.items.size();
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
+            if (live(b))
+                for (int I = 0; I < t.batches[b].nrb; I++) t.items.push_back(WorkItem{b, (short)I, 0});
+        wv.nphi = (long long)t.items.size() - wv.phi0;
+        wv.h0 = (long long)t.items.size();
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
+            if (live(b))
+                for (int I = 0; I < t.batches[b].nrb; I++)
+                    for (int J = I; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)I, (short)J});
+        wv.nh = (long long)t.items.size() - wv.h0;
+        wv.g0 = (long long)t.items.size();
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
+            if (live(b))
+                for (int J = 0; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)J, 0});
+        wv.ng = (long long)t.items.size() - wv.g0;
+        wv.pc0 = (long long)t.items.size();
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
+            if (live(b))
+                for (int c = 0; c < t.batches[b].nc_alloc; c++) t.items.push_back(WorkItem{b, (short)c, 0});
+        wv.npc = (long long)t.items.size() - wv.pc0;
+        wv.d0 = (long long)t.items.size();
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
+            if (!live(b)) continue;
+            for (int mt = 0; mt < t.batches[b].nc_alloc / 2; mt++) t.items.push_back(WorkItem{b, (short)mt, 0});
+        }
+        wv.nd = (long long)t.items.size() - wv.d0;
+        for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
+            const double P = in.batches[b].np, n = in.batches[b].nfn;
+            wv.phi_flops += 30.0 * P * n;
+            wv.phi_bytes += 32.0 * P + 12.0 * P * n;
+            wv.h_flops += P * n * (n + 1.0);
+            wv.h_bytes += 16.0 * n * (n + 1) / 2 + 12.0 * P * n;
+            wv.n_flops += 2.0 * P * n * n + 2.0 * P * n;
+            wv.n_bytes += 6.0 * n * n + 6.0 * P * n + 16.0 * P;
+            wv.g_bytes += 8.0 * n * n + 6.0 * n * n;
+        }
+    }
+    t.ws_bytes = max_ws + 1024;
+    // items must not be empty for the device copy
+    if (!in.host_only) {
+        const size_t nb_bytes = t.batches.size() * sizeof(TcBatch);
+        const size_t ni_bytes = t.items.size() * sizeof(WorkItem);
+        const size_t tot = ((nb_bytes + 255) / 256) * 256 + ni_bytes + 256;
+        cudaError_t e = cudaMalloc(&t.d_mem, tot);
+        if (e != cudaSuccess) {
+            t.d_mem = nullptr;
+            *err = std::string("tensor-core plan: cudaMalloc failed: ") + cudaGetErrorString(e);
+            return FGI_ERR_NOMEM;
+        }
+        char *base = (char *)t.d_mem;
+        if (nb_bytes) cudaMemcpy(base, t.batches.data(), nb_bytes, cudaMemcpyHostToDevice);
+        const size_t ioff = ((nb_bytes + 255) / 256) * 256;
+        if (ni_bytes) cudaMemcpy(base + ioff, t.items.data(), ni_bytes, cudaMemcpyHostToDevice);
+        t.d_batches = (const TcBatch *)base;
+        t.d_items = (const WorkItem *)(base + ioff);
+        e = set_attrs();
+        if (e != cudaSuccess) {
+            *err = std::string("tensor-core plan: cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return FGI_ERR_CUDA;
+        }
+    }
+    t.built = true;
+    return FGI_OK;
+}
+
+void tc_free(TcPlan &t)
+{
+    if (t.d_mem) cudaFree(t.d_mem);
+    t.d_mem = nullptr;
+    t.d_batches = nullptr;
+    t.d_items = nullptr;
+    t.built = false;
+}
+
+size_t tc_workspace_bytes(const TcPlan &t) { return t.ws_bytes; }
+
+cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *v, void *ws,
+                          int n_split, cudaStream_t s)
+{
+    if (w.nphi <= 0) return cudaSuccess;
+    // the H images (v given) of the split mode use the fixed-point leading term
+    const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
+    k_tc_phi<<<(unsigned)w.nphi, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0, (uint8_t *)ws, v,
+                                                       n_split, fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &w, void *ws, int n_split,
+                               cudaStream_t s)
+{
+    if (w.npc <= 0) return cudaSuccess;
+    k_tc_phi_cols<<<(unsigned)w.npc, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0, (uint8_t *)ws,
+                                                           n_split);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, double *h,
+                        int n_split, cudaStream_t s)
+{
+    if (w.nh <= 0) return cudaSuccess;
+    k_tc_h<<<(unsigned)w.nh, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.h0,
+                                                                 (const uint8_t *)ws, h, n_split);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *d,
+                               double offdiag_scale, void *ws, int n_split, cudaStream_t s)
+{
+    if (w.ng <= 0) return cudaSuccess;
+    k_tc_gather_d<<<(unsigned)w.ng, 256, 0, s>>>(P, t.d_batches, t.d_items + w.g0, (uint8_t *)ws, d,
+                                                 offdiag_scale, n_split);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, double *n,
+                              int n_split, cudaStream_t s)
+{
+    if (w.nd <= 0) return cudaSuccess;
+    k_tc_density<<<(unsigned)w.nd, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.d0,
+                                                                       (const uint8_t *)ws, n, n_split);
+    return cudaGetLastError();
 }
 
 }  // namespace fgi

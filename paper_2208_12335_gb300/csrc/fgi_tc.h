@@ -1,4 +1,12 @@
-// Tensor-core (tcgen05) path: plan and call sequences.
+// Tensor-core (tcgen05) path: operand images, work lists, waves, launchers.
+//
+// Per batch b (P_b points, n_b active functions) the basis values are
+// written once per call into "operand images": BF16 planes of the 3-term
+// split phi = x0 + x1 + x2, laid out exactly as the tcgen05 shared-memory
+// operand (128-byte swizzled, K-major rows of 64 points, 1 KB atoms of 8
+// rows, 16 KB chunks of 128 rows), so that one bulk copy moves one operand
+// chunk.  Batches are processed in waves whose images fit a bounded
+// workspace (and stay in L2 when the wave is small).
 #pragma once
 #include <cstddef>
 #include <string>
@@ -7,6 +15,30 @@
 #include "fgi_internal.h"
 
 namespace fgi {
+
+constexpr int kChunkBytes = 16384;       // 128 rows x 64 columns x 2 bytes
+
+struct TcBatch {
+    long long img_phi;     // byte offset (in the wave's workspace) of the phi image
+    long long img_aux;     // byte offset of the w v phi image (H) or the D image (density)
+    long long plane_phi;   // bytes per plane of the phi / w v phi images
+    long long plane_d;     // bytes per plane of the D image
+    int nrb;               // 128-row blocks (functions)
+    int nc;                // 64-point chunks holding points
+    int nc_alloc;          // allocated 64-point chunks (even)
+    int nkc;               // 64-function chunks (density contraction depth)
+};
+
+struct TcWave {
+    int b0 = 0, nb = 0;
+    long long phi0 = 0, nphi = 0;    // items: (batch, row block)
+    long long h0 = 0, nh = 0;        // items: (batch, I, J), I <= J
+    long long g0 = 0, ng = 0;        // items: (batch, J) of the D gather
+    long long pc0 = 0, npc = 0;      // items: (batch, 64-point chunk) of the density's phi image
+    long long d0 = 0, nd = 0;        // items: (batch, point tile of 128)
+    double phi_flops = 0, phi_bytes = 0, h_flops = 0, h_bytes = 0, n_flops = 0, n_bytes = 0;
+    double g_bytes = 0;
+};
 
 struct TcPlanInput {
     int n_batch = 0;
@@ -20,15 +52,29 @@ struct TcPlanInput {
 struct TcPlan {
     bool built = false;
     size_t ws_bytes = 0;
-    void *d_mem = nullptr;               // device tables of this path
+    size_t wave_cap = 0;
+    std::vector<TcBatch> batches;
+    std::vector<WorkItem> items;
+    std::vector<TcWave> waves;
+    void *d_mem = nullptr;               // device copies of batches + items
+    const TcBatch *d_batches = nullptr;
+    const WorkItem *d_items = nullptr;
 };
 
 int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err);
 void tc_free(TcPlan &t);
 size_t tc_workspace_bytes(const TcPlan &t);
-int tc_integrate_h(TcPlan &t, const DevPlan &P, int n_split, const double *v, double *h, void *ws,
-                   cudaStream_t s, std::string *err);
-int tc_density(TcPlan &t, const DevPlan &P, int n_split, const double *d, double offdiag_scale,
-               double *n, void *ws, cudaStream_t s, std::string *err);
+
+// launchers (one wave each); n_split = 3 (split BF16) or 1 (plain BF16)
+cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *v,
+                          void *ws, int n_split, cudaStream_t s);
+cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &w, void *ws, int n_split,
+                               cudaStream_t s);
+cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
+                        double *h, int n_split, cudaStream_t s);
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *d,
+                               double offdiag_scale, void *ws, int n_split, cudaStream_t s);
+cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
+                              double *n, int n_split, cudaStream_t s);
 
 }  // namespace fgi

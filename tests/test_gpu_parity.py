@@ -7,7 +7,7 @@ are compared element by element on the stored pattern (H), point by point
 * FP64 path: 1e-11 relative to max|H| (rounding order only).
 * split BF16: max |dH_ij| <= 1e-7 Ha and density relative L2 <= 1e-7 (the
   accuracy targets the method sets for the split contractions).
-* plain BF16: max |dH_ij| <= 5e-3 Ha (reported, a sanity bound only).
+* plain BF16: max |dH_ij| <= 2e-2 Ha (reported, a sanity bound only).
 """
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-11
 TOL_SPLIT_H = 1e-7
 TOL_SPLIT_N = 1e-7
-TOL_BF16_H = 5e-3
+TOL_BF16_H = 2e-2
 
 
 @pytest.fixture(scope="module")
