@@ -226,6 +226,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
     ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
+    ap.add_argument("--batches", type=int, default=0,
+                    help="use a seeded subset of this many batches (small cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -247,6 +249,11 @@ def main():
     from paper_2208_12335_gb300 import Context
 
     prob, desc = make_workload(args.workload)
+    if args.batches:
+        ids = np.sort(np.random.default_rng(99).choice(prob.n_batch, size=min(args.batches, prob.n_batch),
+                                                        replace=False))
+        prob = prob.subgrid(ids)
+        desc += " (subset: %d seeded batches)" % len(ids)
     D = density_matrix(prob, W.rng_for(1, W.PURPOSE_D))
     t0 = time.perf_counter()
     ctx = Context(local).load(prob, args.precision)

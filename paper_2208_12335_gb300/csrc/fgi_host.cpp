@@ -544,9 +544,13 @@ struct ProfScope {
         : c(c_), s(s_), kind(kind_), flops(f), bytes(by)
     {
         if (!c->prof_on) return;
-        if (c->ev_used + 2 > c->ev_pool.size()) {
-            c->prof_dropped++;
-            return;
+        while (c->ev_used + 2 > c->ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                c->prof_dropped++;
+                return;
+            }
+            c->ev_pool.push_back(e);
         }
         a = c->ev_pool[c->ev_used++];
         b = c->ev_pool[c->ev_used++];
@@ -965,7 +969,7 @@ int fgi_profile(fgi_ctx *c, int enable)
     if (rc) return rc;
     DeviceGuard g(c->device);
     if (enable) {
-        while (c->ev_pool.size() < 16384) {
+        while (c->ev_pool.size() < 1024) {
             cudaEvent_t e;
             CUDA_TRY(c, cudaEventCreate(&e));
             c->ev_pool.push_back(e);
