@@ -354,6 +354,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         tin.act = c->act.data();
         tin.atom_nfn = c->atom_nfn.data();
         tin.tune_path = tune_path;
+        tin.nnz = c->nnz;
         tin.host_only = true;
         std::string terr;
         int rc = tc_build(c->tc, tin, &terr);
@@ -501,6 +502,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     tin.act = c->act.data();
     tin.atom_nfn = c->atom_nfn.data();
     tin.tune_path = tune_path;
+    tin.nnz = c->nnz;
     std::string terr;
     int rc = tc_build(c->tc, tin, &terr);
     if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
@@ -828,8 +830,8 @@ int fgi_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void
     if ((rc = check_ws(c, ws, ws_bytes))) return rc;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!accumulate) CUDA_TRY(c, cudaMemsetAsync(h, 0, (size_t)c->nnz * sizeof(double), s));
     if (c->precision == FGI_FP64) {
+        if (!accumulate) CUDA_TRY(c, cudaMemsetAsync(h, 0, (size_t)c->nnz * sizeof(double), s));
         DevPlan P = c->dp;
         P.batches = c->d_batches_f64;
         for (const Wave &w : c->waves) {
@@ -845,13 +847,18 @@ int fgi_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void
     const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
     DevPlan P = c->dp;
     P.batches = c->d_batches_f64;
+    CUDA_TRY(c, cudaMemsetAsync(ws, 0, (size_t)c->nnz * 8, s));       // fixed-point accumulator
     for (const TcWave &w : c->tc.waves) {
         {
             ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
             CUDA_TRY(c, tc_launch_phi(c->tc, P, w, v, ws, n_split, s));
         }
         ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
-        CUDA_TRY(c, tc_launch_h(c->tc, P, w, ws, h, n_split, s));
+        CUDA_TRY(c, tc_launch_h(c->tc, P, w, ws, n_split, s));
+    }
+    {
+        ProfScope ps(c, s, 4, 2.0 * c->nnz, 24.0 * c->nnz);
+        CUDA_TRY(c, tc_launch_fix_to_h(c->tc, ws, h, c->nnz, accumulate, s));
     }
     return FGI_OK;
 }
@@ -880,6 +887,10 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
         }
     } else {
         const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+        {
+            ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz);
+            CUDA_TRY(c, tc_launch_to_df(d, ws, c->nnz, s));
+        }
         for (const TcWave &w : c->tc.waves) {
             {
                 ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
@@ -887,7 +898,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
             }
             {
                 ProfScope ps(c, s, 4, 0.0, w.g_bytes);
-                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, d, 1.0, ws, n_split, s));
+                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, ws, 1.0, ws, n_split, s));
             }
             ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
             CUDA_TRY(c, tc_launch_density(c->tc, P, w, ws, n, n_split, s));

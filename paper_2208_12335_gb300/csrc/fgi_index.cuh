@@ -18,8 +18,11 @@ __device__ __forceinline__ int find_act(const DevAct *act, int n, int l)
 
 struct FnRef {
     long long gi;   // global function
+    long long rp;   // index of the first stored value of row gi
     int atom;       // global atom
     int li;         // index inside the atom
+    int loc;        // atom index inside its system
+    int pad;
 };
 
 __device__ __forceinline__ FnRef fn_ref(const DevPlan &P, const DevAct *act, int e, int l)
@@ -29,7 +32,19 @@ __device__ __forceinline__ FnRef fn_ref(const DevPlan &P, const DevAct *act, int
     r.atom = A.atom;
     r.li = l - A.fn_loc;
     r.gi = P.atom_fn0[A.atom] + r.li;
+    r.rp = P.rowptr[r.gi];
+    r.loc = P.atom_loc[A.atom];
+    r.pad = 0;
     return r;
+}
+
+// value_index with the system's pair table and atom count already looked up
+__device__ __forceinline__ long long value_index_pp(const int *pairpos_sys, int nat, const FnRef &a, const FnRef &b)
+{
+    if (a.atom == b.atom) return a.rp + (b.gi - a.gi);
+    const int pp = __ldg(pairpos_sys + (long long)a.loc * nat + b.loc);
+    if (pp < 0) return -1;
+    return a.rp + pp - a.li + b.li;
 }
 
 // Stored value of (a, b), a.gi <= b.gi.  Row a.gi holds first the rest of its
@@ -39,12 +54,7 @@ __device__ __forceinline__ FnRef fn_ref(const DevPlan &P, const DevAct *act, int
 __device__ __forceinline__ long long value_index(const DevPlan &P, int sys, const FnRef &a,
                                                  const FnRef &b)
 {
-    long long rp = P.rowptr[a.gi];
-    if (a.atom == b.atom) return rp + (b.gi - a.gi);
-    int nat = P.sys_nat[sys];
-    int pp = P.pairpos[P.sys_pair_off[sys] + (long long)P.atom_loc[a.atom] * nat + P.atom_loc[b.atom]];
-    if (pp < 0) return -1;
-    return rp + pp - a.li + b.li;
+    return value_index_pp(P.pairpos + P.sys_pair_off[sys], P.sys_nat[sys], a, b);
 }
 
 }  // namespace fgi

@@ -186,33 +186,6 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// x = x0 + x1 + x2 with each term BF16, rounded to nearest in turn.
-__device__ __forceinline__ void split3(double x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
-{
-    a = __double2bfloat16(x);
-    double r = x - (double)__bfloat162float(a);
-    b = __double2bfloat16(r);
-    r -= (double)__bfloat162float(b);
-    c = __double2bfloat16(r);
-}
-
-__device__ __forceinline__ void store_split8d(uint8_t *dst, long long plane, const double *x, int n_split)
-{
-    uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-        split3(x[2 * q], a0, a1, a2);
-        split3(x[2 * q + 1], b0, b1, b2);
-        w0[q] = pack_bf16(a0, b0);
-        w1[q] = pack_bf16(a1, b1);
-        w2[q] = pack_bf16(a2, b2);
-    }
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    if (n_split > 1) *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    if (n_split > 2) *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-}
-
 // byte offset of the 16-byte unit (row r, 8-column group g) inside chunk (blk, c)
 __device__ __forceinline__ long long unit_offset(int blk, int nchunk, int c, int r, int g)
 {
@@ -344,7 +317,10 @@ __device__ __forceinline__ int fixed_bits(int depth)
     return b;
 }
 
-__device__ __forceinline__ void fixed_scale(float mx, int bits, float &scale, float &unit)
+// Leading-digit width: 8 bits when the row's sum S = sum|x|/2^e <= 200 (then
+// every row-pair sum stays below 65536 S + 128 K < 2^24 for K <= 8192),
+// otherwise the width that keeps depth x 2^(2b) <= 2^24.
+__device__ __forceinline__ void fixed_scale_adaptive(float mx, float sum, int depth, float &scale, float &unit)
 {
     if (!(mx > 1e-30f)) {
         scale = 0.f;
@@ -353,9 +329,12 @@ __device__ __forceinline__ void fixed_scale(float mx, int bits, float &scale, fl
     }
     int e;
     frexpf(mx * (1.f + 1.f / 4096.f), &e);
+    const float S = ldexpf(sum, -e) * 1.001f;
+    const int bits = (S <= 200.f) ? 8 : fixed_bits(depth);
     scale = ldexpf(1.f, bits - e);
     unit = ldexpf(1.f, e - bits);
 }
+
 
 // FP32 phi of one atom's functions at one point (first pass of the H images:
 // only the row maxima are taken from it)
@@ -374,16 +353,16 @@ __device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const flo
     return r;
 }
 
-constexpr int kPhiValStride = 65;   // float2 per row of phi_smem (padding against bank conflicts)
+constexpr int kPhiValStride = 33;   // float2 per row of phi_smem (32 points + padding)
 
 // Double-float phi for rows [r0, r0+128) (atoms e0..e0+ne-1 of the batch)
-// at the 64 points of chunk c, into phi_smem[row - r0][point] (zero for
+// at the 32 points p0..p0+31, into phi_smem[row - r0][point - p0] (zero for
 // points beyond the batch).
 __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatch &B, const DevAct *act, int e0,
-                                                 int ne, int r0, int c, float2 *phi_smem)
+                                                 int ne, int r0, int p0, float2 *phi_smem)
 {
-    for (int u = threadIdx.x; u < ne * 64; u += blockDim.x) {
-        const int e = e0 + (u >> 6), k = u & 63, p = c * 64 + k;
+    for (int u = threadIdx.x; u < ne * 32; u += blockDim.x) {
+        const int e = e0 + (u >> 5), k = u & 31, p = p0 + k;
         const DevAct A = act[e];
         const DevSpecies S = P.species[P.atom_species[A.atom]];
         const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
@@ -458,8 +437,9 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
                                                 uint8_t *ws, const double *v, int n_split, int fixed)
 {
     extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
-    __shared__ float2 wv[64];
+    __shared__ float2 wv[32];
     __shared__ unsigned int rowmax[2][128];          // |phi|, |w v phi| maxima (float bits)
+    __shared__ float rowsum[2][128];                 // sums of |phi|, |w v phi| over the points
     __shared__ float fsc[2][128][2];                 // per row: scale, unit
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
@@ -475,7 +455,10 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
     uint8_t *a_img = ws + T.img_aux;
     if (fixed) {
         // pass 1: row maxima of |phi| and |w v phi| over the batch's points (FP32)
-        for (int q = threadIdx.x; q < 256; q += blockDim.x) (&rowmax[0][0])[q] = 0u;
+        for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+            (&rowmax[0][0])[q] = 0u;
+            (&rowsum[0][0])[q] = 0.f;
+        }
         __syncthreads();
         const int units = ne * 64 * T.nc;
         for (int u0 = 0; u0 < units; u0 += blockDim.x) {
@@ -511,14 +494,23 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
                 ylm_poly_f32(R.l, x, y, z, Q, ci);
                 for (int m = 0; m < nm; m++, f++) {
                     float a = fabsf(rad * kYlmC[ci[m]].x * Q[m]);
-                    if (!(a < 3.0e38f)) a = 3.0e38f;           // non-finite input: keep the scale finite
-                    unsigned int mp = __float_as_uint(a), ma = __float_as_uint(fminf(a * wvp, 3.0e38f));
+                    if (!(a < 1.0e30f)) a = 1.0e30f;           // non-finite input: keep the scale finite
+                    const float aw = fminf(a * wvp, 1.0e30f);
+                    unsigned int mp = __float_as_uint(a), ma = __float_as_uint(aw);
+                    float sp = a, sa = aw;
                     // a warp holds 32 consecutive points of one atom and chunk
                     mp = __reduce_max_sync(0xffffffffu, mp);
                     ma = __reduce_max_sync(0xffffffffu, ma);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+                        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                    }
                     if ((threadIdx.x & 31) == 0 && f >= f_lo && f < f_hi) {
                         atomicMax(&rowmax[0][A.fn_loc + f - r0], mp);
                         atomicMax(&rowmax[1][A.fn_loc + f - r0], ma);
+                        atomicAdd(&rowsum[0][A.fn_loc + f - r0], sp);
+                        atomicAdd(&rowsum[1][A.fn_loc + f - r0], sa);
                     }
                 }
             }
@@ -527,16 +519,17 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
         if (threadIdx.x < 256) {
             const int which = threadIdx.x >> 7, r = threadIdx.x & 127;
             float sc, un;
-            fixed_scale(__uint_as_float(rowmax[which][r]), fixed_bits(T.nc * 64), sc, un);
+            fixed_scale_adaptive(__uint_as_float(rowmax[which][r]), rowsum[which][r], T.nc * 64, sc, un);
             fsc[which][r][0] = sc;
             fsc[which][r][1] = un;
         }
         __syncthreads();
     }
-    for (int c = 0; c < T.nc_alloc; c++) {
-        eval_block_chunk(P, B, act, e0, ne, r0, c, phi_smem);
-        if (threadIdx.x < 64) {
-            const int p = c * 64 + threadIdx.x;
+    for (int c2 = 0; c2 < 2 * T.nc_alloc; c2++) {
+        const int c = c2 >> 1, half = c2 & 1;
+        eval_block_chunk(P, B, act, e0, ne, r0, c * 64 + half * 32, phi_smem);
+        if (threadIdx.x < 32) {
+            const int p = c * 64 + half * 32 + threadIdx.x;
             double s = 0.0;
             if (v && p < B.np) {
                 const double vv = v[B.pt0 + p];
@@ -547,13 +540,13 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
             wv[threadIdx.x] = make_float2(sd.hi, sd.lo);
         }
         __syncthreads();
-        for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
-            const int r = u >> 3, g = u & 7;
+        for (int u = threadIdx.x; u < 512; u += blockDim.x) {
+            const int r = u >> 2, gg = u & 3, g = half * 4 + gg;
             const bool live = r0 + r < B.nfn;
             df x[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const float2 t = live ? phi_smem[r * kPhiValStride + g * 8 + q] : make_float2(0.f, 0.f);
+                const float2 t = live ? phi_smem[r * kPhiValStride + gg * 8 + q] : make_float2(0.f, 0.f);
                 x[q] = df{t.x, t.y};
             }
             const long long off = unit_offset(I, T.nc_alloc, c, r, g);
@@ -564,7 +557,7 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
             if (v) {
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    const float2 s = wv[g * 8 + q];
+                    const float2 s = wv[gg * 8 + q];
                     x[q] = df_mul(x[q], df{s.x, s.y});
                 }
                 if (fixed)
@@ -586,6 +579,7 @@ __global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *t
 {
     extern __shared__ float2 phi_smem[];
     __shared__ unsigned int colmax[64];
+    __shared__ float colsum[64];
     __shared__ float csc[2][64];
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
@@ -595,7 +589,10 @@ __global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *t
     uint8_t *phi_img = ws + T.img_phi;
     const bool fixed = n_split == 3;
     if (fixed) {
-        if (threadIdx.x < 64) colmax[threadIdx.x] = 0u;
+        if (threadIdx.x < 64) {
+            colmax[threadIdx.x] = 0u;
+            colsum[threadIdx.x] = 0.f;
+        }
         __syncthreads();
         for (int u = threadIdx.x; u < B.n_act * 64; u += blockDim.x) {
             const int e = u >> 6, k = u & 63, p = c * 64 + k;
@@ -608,41 +605,48 @@ __global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *t
             const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
             const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
             const float d = sqrtf(x * x + y * y + z * z);
-            float mx = 0.f;
+            float mx = 0.f, sm = 0.f;
             for (int sh = 0; sh < S.n_shell; sh++) {
                 const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
                 const float rad = radial_over_d_f32(R, P.coef_dd, d);
                 float Q[7];
                 int ci[7];
                 ylm_poly_f32(R.l, x, y, z, Q, ci);
-                for (int m = 0; m < 2 * R.l + 1; m++) mx = fmaxf(mx, fabsf(rad * kYlmC[ci[m]].x * Q[m]));
+                for (int m = 0; m < 2 * R.l + 1; m++) {
+                    const float a = fabsf(rad * kYlmC[ci[m]].x * Q[m]);
+                    mx = fmaxf(mx, a);
+                    sm += a;
+                }
             }
-            if (!(mx < 3.0e38f)) mx = 3.0e38f;
+            if (!(mx < 1.0e30f)) mx = 1.0e30f;
+            if (!(sm < 1.0e30f)) sm = 1.0e30f;
             atomicMax(&colmax[k], __float_as_uint(mx));
+            atomicAdd(&colsum[k], sm);
         }
         __syncthreads();
         if (threadIdx.x < 64) {
             float sc, un;
-            fixed_scale(__uint_as_float(colmax[threadIdx.x]), fixed_bits(T.nkc * 64), sc, un);
+            fixed_scale_adaptive(__uint_as_float(colmax[threadIdx.x]), colsum[threadIdx.x], T.nkc * 64, sc, un);
             csc[0][threadIdx.x] = sc;
             csc[1][threadIdx.x] = un;
         }
         __syncthreads();
     }
-    for (int I = 0; I < T.nrb; I++) {
+    for (int I2 = 0; I2 < 2 * T.nrb; I2++) {
+        const int I = I2 >> 1, half = I2 & 1;
         const int r0 = I * 128;
         const int rend = min(r0 + 128, B.nfn);
         const int e0 = find_act(act, B.n_act, r0);
         const int e1 = find_act(act, B.n_act, rend - 1);
-        eval_block_chunk(P, B, act, e0, e1 - e0 + 1, r0, c, phi_smem);
+        eval_block_chunk(P, B, act, e0, e1 - e0 + 1, r0, c * 64 + half * 32, phi_smem);
         __syncthreads();
-        for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
-            const int r = u >> 3, g = u & 7;
+        for (int u = threadIdx.x; u < 512; u += blockDim.x) {
+            const int r = u >> 2, gg = u & 3, g = half * 4 + gg;
             const bool live = r0 + r < B.nfn;
             df x[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const float2 t = live ? phi_smem[r * kPhiValStride + g * 8 + q] : make_float2(0.f, 0.f);
+                const float2 t = live ? phi_smem[r * kPhiValStride + gg * 8 + q] : make_float2(0.f, 0.f);
                 x[q] = df{t.x, t.y};
             }
             const long long off = unit_offset(I, T.nc_alloc, c, r, g);
@@ -652,6 +656,41 @@ __global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *t
                 store_split8_df(phi_img + off, T.plane_phi, x, n_split);
         }
         __syncthreads();
+    }
+}
+
+// FP32 value -> signed fixed point with unit 2^-40 (round to nearest), from
+// the IEEE bit pattern with integer operations only.  |f| must stay below
+// 2^22; larger or non-finite values set *bad.
+constexpr int kFixBits = 40;
+
+__device__ __forceinline__ long long f32_to_fix(float f, bool &bad)
+{
+    const unsigned u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFFu);
+    if (e == 0) return 0;                                   // zero or below 1.2e-38
+    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150 + kFixBits;                      // f = m 2^(e-150)
+    long long r;
+    if (sh > 38) {
+        bad = true;
+        r = 0;
+    } else if (sh >= 0) {
+        r = m << sh;
+    } else if (sh > -25) {
+        r = (m + (1ll << (-sh - 1))) >> -sh;
+    } else {
+        r = 0;
+    }
+    return (u >> 31) ? -r : r;
+}
+
+// h[k] = (accumulate ? h[k] : 0) + acc[k] 2^-40
+__global__ void k_fix_to_h(const long long *acc, double *h, long long n, int accumulate)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double v = (double)acc[k] * 0x1p-40;
+        h[k] = accumulate ? h[k] + v : v;
     }
 }
 
@@ -669,7 +708,7 @@ struct TcSmem {
 };
 
 __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                        const uint8_t *ws, double *h, int n_split)
+                                                        const uint8_t *ws, unsigned long long *hfix, int n_split)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -763,7 +802,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch
         const bool row_ok = ok && i < B.nfn;
         FnRef rref{};
         if (row_ok) rref = fn_ref(P, act, find_act(act, B.n_act, i), i);
+        const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
+        const int nat = P.sys_nat[B.sys];
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        bool bad = false;
         for (int cc = 0; cc < 4; cc++) {
             if (j0 + cc * 32 >= B.nfn) break;
             float a0[32], a1[32];
@@ -776,11 +818,13 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch
                 const int jl = cc * 32 + q;
                 const int j = j0 + jl;
                 if (j >= B.nfn || i > j) continue;
-                const double val = (double)a0[q] + (n_split > 1 ? (double)a1[q] : 0.0);
-                const long long k = value_index(P, B.sys, rref, S->ref[jl]);
-                if (k >= 0) atomicAdd(h + k, val);
+                long long fx = f32_to_fix(a0[q], bad);
+                if (n_split > 1) fx += f32_to_fix(a1[q], bad);
+                const long long k = value_index_pp(pp_sys, nat, rref, S->ref[jl]);
+                if (k >= 0 && fx != 0) atomicAdd(hfix + k, (unsigned long long)fx);
             }
         }
+        if (bad) atomicOr(P.status, kStatusNonFinite);
     }
     tc_fence_before();
     __syncthreads();
@@ -793,19 +837,30 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch
 // K-major swizzled image.  In the split mode the leading term is fixed-point
 // on a per-row grid (the density contracts over i), found by a first pass
 // over the row block.
-__device__ __forceinline__ double gather_d_value(const DevPlan &P, const DevBatch &B, const FnRef &rj,
-                                                 const FnRef &ci, int j, int i, const double *dval,
-                                                 double offdiag_scale)
+__device__ __forceinline__ df gather_d_value(const int *pp_sys, int nat, int nfn, const FnRef &rj, const FnRef &ci,
+                                             int j, int i, const float2 *ddv, float offdiag_scale)
 {
-    if (j >= B.nfn || i >= B.nfn) return 0.0;
+    if (j >= nfn || i >= nfn) return df{0.f, 0.f};
     const FnRef &a = (i <= j) ? ci : rj;
     const FnRef &b = (i <= j) ? rj : ci;
-    const long long k = value_index(P, B.sys, a, b);
-    return k >= 0 ? __ldg(dval + k) * (i == j ? 1.0 : offdiag_scale) : 0.0;
+    const long long k = value_index_pp(pp_sys, nat, a, b);
+    if (k < 0) return df{0.f, 0.f};
+    const float2 v = __ldg(ddv + k);
+    const float sc = i == j ? 1.f : offdiag_scale;     // 1 or 1/2: exact
+    return df{v.x * sc, v.y * sc};
+}
+
+// D values as double-floats (once per density call; nnz elements)
+__global__ void k_to_df(const double *x, float2 *out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const df v = df_from_double(x[k]);
+        out[k] = make_float2(v.hi, v.lo);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                     uint8_t *ws, const double *dval, double offdiag_scale,
+                                                     uint8_t *ws, const float2 *ddv, float offdiag_scale,
                                                      int n_split)
 {
     const WorkItem it = items[blockIdx.x];
@@ -814,13 +869,17 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
     const int J = it.ti;
     __shared__ FnRef rref[128], cref[64];
     __shared__ unsigned int rowmax[128];
+    __shared__ float rowsum[128];
     __shared__ float rsc[2][128];
     const DevAct *act = P.act + B.act0;
     const bool fixed = n_split == 3;
+    const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
+    const int nat = P.sys_nat[B.sys];
     if (threadIdx.x < 128) {
         const int j = J * 128 + threadIdx.x;
         if (j < B.nfn) rref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, j), j);
         rowmax[threadIdx.x] = 0u;
+        rowsum[threadIdx.x] = 0.f;
     }
     uint8_t *img = ws + T.img_aux;
     for (int pass = fixed ? 0 : 1; pass < 2; pass++) {
@@ -828,7 +887,7 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
             __syncthreads();
             if (threadIdx.x < 128) {
                 float sc, un;
-                fixed_scale(__uint_as_float(rowmax[threadIdx.x]), fixed_bits(T.nkc * 64), sc, un);
+                fixed_scale_adaptive(__uint_as_float(rowmax[threadIdx.x]), rowsum[threadIdx.x], T.nkc * 64, sc, un);
                 rsc[0][threadIdx.x] = sc;
                 rsc[1][threadIdx.x] = un;
             }
@@ -843,29 +902,30 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
             for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
                 const int r = u >> 3, g = u & 7;
                 const int j = J * 128 + r;
-                double x[8];
+                df x[8];
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const int il = g * 8 + q;
-                    x[q] = gather_d_value(P, B, rref[r], cref[il], j, kc * 64 + il, dval, offdiag_scale);
+                    x[q] = gather_d_value(pp_sys, nat, B.nfn, rref[r], cref[il], j, kc * 64 + il, ddv, offdiag_scale);
                 }
                 if (pass == 0) {
-                    float mx = 0.f;
+                    float mx = 0.f, sm = 0.f;
 #pragma unroll
-                    for (int q = 0; q < 8; q++) mx = fmaxf(mx, fabsf((float)x[q]));
-                    if (!(mx < 3.0e38f)) mx = 3.0e38f;
+                    for (int q = 0; q < 8; q++) {
+                        mx = fmaxf(mx, fabsf(x[q].hi));
+                        sm += fabsf(x[q].hi);
+                    }
+                    if (!(mx < 1.0e30f)) mx = 1.0e30f;
+                    if (!(sm < 1.0e30f)) sm = 1.0e30f;
                     atomicMax(&rowmax[r], __float_as_uint(mx));
+                    atomicAdd(&rowsum[r], sm);
                     continue;
                 }
                 uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
-                if (fixed) {
-                    df xd[8];
-#pragma unroll
-                    for (int q = 0; q < 8; q++) xd[q] = df_from_double(x[q]);
-                    store_fixed8(dst, T.plane_d, xd, rsc[0][r], rsc[1][r]);
-                } else {
-                    store_split8d(dst, T.plane_d, x, n_split);
-                }
+                if (fixed)
+                    store_fixed8(dst, T.plane_d, x, rsc[0][r], rsc[1][r]);
+                else
+                    store_split8_df(dst, T.plane_d, x, n_split);
             }
         }
     }
@@ -990,60 +1050,58 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_density(DevPlan P, const T
             for (int cc = 0; cc < 4; cc++) {
                 float a0[32], a1[32];
                 tmem_ld32(tmem + lane_base + cc * 32, a0);
-                if (n_split > 1) tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
+                if (n_split > 1)
+                    tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
+                else
+#pragma unroll
+                    for (int q = 0; q < 32; q++) a1[q] = 0.f;
                 tmem_wait_ld();
                 if (cc == 3) {
                     tc_fence_before();
                     mbar_arrive(&S->acc_empty);   // accumulator may be overwritten
                 }
-                // phi_j(p) for the 32 points of this column chunk
+                // E^T[j][p] phi_j(p) for the 32 points of this column chunk in
+                // double-float (FP32 pipe): e = acc0 + acc1, phi = sum of its planes
                 const int c = 2 * m + (cc >> 1);
-                double prod[32];
+                const bool live = ok && j < B.nfn;
 #pragma unroll
                 for (int gg = 0; gg < 4; gg++) {
                     const int g = (cc & 1) * 4 + gg;
                     const long long off = unit_offset(J, T.nc_alloc, c, r, g);
-                    float ph[8];
-                    {
-                        const uint4 u0 = *reinterpret_cast<const uint4 *>(phi_img + off);
-                        const uint32_t w0[4] = {u0.x, u0.y, u0.z, u0.w};
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            ph[2 * q] = __uint_as_float(w0[q] << 16);
-                            ph[2 * q + 1] = __uint_as_float(w0[q] & 0xFFFF0000u);
-                        }
-                    }
-                    double phd[8];
-#pragma unroll
-                    for (int q = 0; q < 8; q++) phd[q] = (double)ph[q];
-                    for (int s = 1; s < n_split; s++) {
-                        const uint4 u1 = *reinterpret_cast<const uint4 *>(phi_img + off + s * T.plane_phi);
-                        const uint32_t w1[4] = {u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            phd[2 * q] += (double)__uint_as_float(w1[q] << 16);
-                            phd[2 * q + 1] += (double)__uint_as_float(w1[q] & 0xFFFF0000u);
-                        }
+                    uint32_t w[3][4] = {};
+                    for (int sp = 0; sp < n_split; sp++) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi);
+                        w[sp][0] = u.x; w[sp][1] = u.y; w[sp][2] = u.z; w[sp][3] = u.w;
                     }
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
                         const int col = gg * 8 + q;
-                        const double e = (double)a0[col] + (n_split > 1 ? (double)a1[col] : 0.0);
-                        prod[col] = (ok && j < B.nfn) ? e * phd[q] : 0.0;
+                        const float f0 = __uint_as_float((q & 1) ? (w[0][q >> 1] & 0xFFFF0000u) : (w[0][q >> 1] << 16));
+                        const float f1 = __uint_as_float((q & 1) ? (w[1][q >> 1] & 0xFFFF0000u) : (w[1][q >> 1] << 16));
+                        const float f2 = __uint_as_float((q & 1) ? (w[2][q >> 1] & 0xFFFF0000u) : (w[2][q >> 1] << 16));
+                        df ph = df_two_sum(f0, f1);
+                        ph = df_fast_two_sum(ph.hi, ph.lo + f2);
+                        const df e = df_two_sum(a0[col], n_split > 1 ? a1[col] : 0.f);
+                        const df pr = df_mul(e, ph);
+                        a0[col] = live ? pr.hi : 0.f;
+                        a1[col] = live ? pr.lo : 0.f;
                     }
                 }
                 // reduce over the 32 lanes (rows j): lane q ends with column q
 #pragma unroll
-                for (int w = 16; w >= 1; w >>= 1) {
-                    const bool upper = (lane & w) != 0;
+                for (int wd = 16; wd >= 1; wd >>= 1) {
+                    const bool upper = (lane & wd) != 0;
 #pragma unroll
-                    for (int q = 0; q < w; q++) {
-                        const double send = upper ? prod[q] : prod[q + w];
-                        const double keep = upper ? prod[q + w] : prod[q];
-                        prod[q] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                    for (int q = 0; q < wd; q++) {
+                        const float sh = upper ? a0[q] : a0[q + wd], sl = upper ? a1[q] : a1[q + wd];
+                        const float kh = upper ? a0[q + wd] : a0[q], kl = upper ? a1[q + wd] : a1[q];
+                        const df rcv{__shfl_xor_sync(0xffffffffu, sh, wd), __shfl_xor_sync(0xffffffffu, sl, wd)};
+                        const df sum = df_add(df{kh, kl}, rcv);
+                        a0[q] = sum.hi;
+                        a1[q] = sum.lo;
                     }
                 }
-                red[warp][cc * 32 + lane] += prod[0];
+                red[warp][cc * 32 + lane] += (double)a0[0] + (double)a1[0];
             }
         }
     }
@@ -1168,7 +1226,10 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
             wv.g_bytes += 8.0 * n * n + 6.0 * n * n;
         }
     }
-    t.ws_bytes = max_ws + 1024;
+    // scratch before the images: the fixed-point H accumulator or the
+    // double-float copy of D (nnz x 8 bytes either way)
+    t.img_base = ((size_t)in.nnz * 8 + 1023) / 1024 * 1024;
+    t.ws_bytes = t.img_base + max_ws + 1024;
     // items must not be empty for the device copy
     if (!in.host_only) {
         const size_t nb_bytes = t.batches.size() * sizeof(TcBatch);
@@ -1213,8 +1274,8 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     if (w.nphi <= 0) return cudaSuccess;
     // the H images (v given) of the split mode use the fixed-point leading term
     const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
-    k_tc_phi<<<(unsigned)w.nphi, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0, (uint8_t *)ws, v,
-                                                       n_split, fixed);
+    k_tc_phi<<<(unsigned)w.nphi, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
+                                                       (uint8_t *)ws + t.img_base, v, n_split, fixed);
     return cudaGetLastError();
 }
 
@@ -1222,26 +1283,43 @@ cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &
                                cudaStream_t s)
 {
     if (w.npc <= 0) return cudaSuccess;
-    k_tc_phi_cols<<<(unsigned)w.npc, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0, (uint8_t *)ws,
-                                                           n_split);
+    k_tc_phi_cols<<<(unsigned)w.npc, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0,
+                                                           (uint8_t *)ws + t.img_base, n_split);
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, double *h,
-                        int n_split, cudaStream_t s)
+cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, int n_split,
+                        cudaStream_t s)
 {
     if (w.nh <= 0) return cudaSuccess;
     k_tc_h<<<(unsigned)w.nh, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.h0,
-                                                                 (const uint8_t *)ws, h, n_split);
+                                                          (const uint8_t *)ws + t.img_base,
+                                                          (unsigned long long *)ws, n_split);
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *d,
+cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long long nnz, int accumulate,
+                               cudaStream_t s)
+{
+    (void)t;
+    if (nnz <= 0) return cudaSuccess;
+    k_fix_to_h<<<1216, 256, 0, s>>>((const long long *)ws, h, nnz, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *d_df,
                                double offdiag_scale, void *ws, int n_split, cudaStream_t s)
 {
     if (w.ng <= 0) return cudaSuccess;
-    k_tc_gather_d<<<(unsigned)w.ng, 256, 0, s>>>(P, t.d_batches, t.d_items + w.g0, (uint8_t *)ws, d,
-                                                 offdiag_scale, n_split);
+    k_tc_gather_d<<<(unsigned)w.ng, 256, 0, s>>>(P, t.d_batches, t.d_items + w.g0, (uint8_t *)ws + t.img_base,
+                                                 (const float2 *)d_df, (float)offdiag_scale, n_split);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_to_df(const double *x, void *out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_to_df<<<1216, 256, 0, s>>>(x, (float2 *)out, n);
     return cudaGetLastError();
 }
 
@@ -1250,7 +1328,7 @@ cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w
 {
     if (w.nd <= 0) return cudaSuccess;
     k_tc_density<<<(unsigned)w.nd, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.d0,
-                                                                       (const uint8_t *)ws, n, n_split);
+                                                                (const uint8_t *)ws + t.img_base, n, n_split);
     return cudaGetLastError();
 }
 

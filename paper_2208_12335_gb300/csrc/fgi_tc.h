@@ -46,6 +46,7 @@ struct TcPlanInput {
     const DevAct *act = nullptr;
     const int *atom_nfn = nullptr;
     const char *tune_path = nullptr;
+    long long nnz = 0;                   // stored values of H (scratch sizing)
     bool host_only = false;              // build host tables only (no device copies)
 };
 
@@ -53,6 +54,7 @@ struct TcPlan {
     bool built = false;
     size_t ws_bytes = 0;
     size_t wave_cap = 0;
+    size_t img_base = 0;                 // workspace offset of the wave images (scratch below)
     std::vector<TcBatch> batches;
     std::vector<WorkItem> items;
     std::vector<TcWave> waves;
@@ -70,9 +72,14 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
                           void *ws, int n_split, cudaStream_t s);
 cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &w, void *ws, int n_split,
                                cudaStream_t s);
-cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
-                        double *h, int n_split, cudaStream_t s);
-cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const double *d,
+// H: accumulates into the 2^-40 fixed-point scratch at the workspace start
+cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, int n_split,
+                        cudaStream_t s);
+cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long long nnz, int accumulate,
+                               cudaStream_t s);
+// density: D converted once to double-floats in the scratch, then gathered per batch
+cudaError_t tc_launch_to_df(const double *x, void *out, long long n, cudaStream_t s);
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *d_df,
                                double offdiag_scale, void *ws, int n_split, cudaStream_t s);
 cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
                               double *n, int n_split, cudaStream_t s);

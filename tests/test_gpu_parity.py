@@ -213,3 +213,19 @@ def test_workspace_errors(fgi, water):
     with pytest.raises(fgi.FGIError) as e:
         ctx.integrate_h(v, ws=small)
     assert e.value.code == -4
+
+
+def test_split_h_is_bitwise_reproducible(fgi, si64_sub):
+    """The split path accumulates H in 2^-40 fixed point (integer atomics):
+    the result does not depend on the order in which tiles land."""
+    prob, _, _, _ = si64_sub
+    ctx = fgi.Context(0).load(prob, "split_bf16")
+    v = dev(prob.v)
+    h1 = ctx.integrate_h(v).clone()
+    h2 = ctx.integrate_h(v).clone()
+    ctx.sync()
+    assert torch.equal(h1, h2)
+    # accumulate = 1 adds onto the previous values
+    h3 = ctx.integrate_h(v, h2.clone(), accumulate=True)
+    ctx.sync()
+    assert torch.allclose(h3, 2 * h1, rtol=0, atol=1e-12)
