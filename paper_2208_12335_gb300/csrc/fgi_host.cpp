@@ -97,7 +97,7 @@ struct fgi_ctx {
     DevPlan dp{};
     DevBatch *d_batches_f64 = nullptr;
     WorkItem *d_items = nullptr;
-    long long *d_sys_val0 = nullptr, *d_sys_fn0 = nullptr;
+    long long *d_sys_val0 = nullptr, *d_sys_fn0 = nullptr, *d_sys_nnz = nullptr;
     int *d_fn_sys = nullptr;
     int *d_status = nullptr;
     TcPlan tc;                                // tensor-core path plan
@@ -355,6 +355,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         tin.atom_nfn = c->atom_nfn.data();
         tin.tune_path = tune_path;
         tin.nnz = c->nnz;
+        tin.n_fn = c->n_fn;
         tin.host_only = true;
         std::string terr;
         int rc = tc_build(c->tc, tin, &terr);
@@ -420,6 +421,20 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     for (int s = 0; s < c->n_sys; s++) sys_nat[s] = (int)(c->atom_off[s + 1] - c->atom_off[s]);
     std::vector<long long> sys_val0(c->sys_val0.begin(), c->sys_val0.end());
     std::vector<long long> sys_fn0(c->sys_fn0.begin(), c->sys_fn0.end());
+    std::vector<long long> sys_nnz(c->sys_nnz.begin(), c->sys_nnz.end());
+    // global column function of every stored value (-1 on the diagonal)
+    std::vector<int> col_glob((size_t)c->nnz);
+    for (int s = 0; s < c->n_sys; s++)
+        for (int64_t a = c->atom_off[s]; a < c->atom_off[s + 1]; a++)
+            for (int li = 0; li < c->atom_nfn[a]; li++) {
+                const long long gi = c->atom_fn0[a] + li;
+                long long k = c->rowptr[gi];
+                for (long long j = gi; j < c->atom_fn0[a] + c->atom_nfn[a]; j++) col_glob[k++] = j == gi ? -1 : (int)j;
+                for (int b : c->nbr[a]) {
+                    if (b == a) continue;
+                    for (int lj = 0; lj < c->atom_nfn[b]; lj++) col_glob[k++] = (int)(c->atom_fn0[b] + lj);
+                }
+            }
 
     struct Blob {
         const void *src;
@@ -453,7 +468,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_act = add(c->act.data(), c->act.size() * sizeof(DevAct)),
            i_items = add(c->items.data(), c->items.size() * sizeof(WorkItem)),
            i_sv0 = add(sys_val0.data(), sys_val0.size() * 8), i_sf0 = add(sys_fn0.data(), sys_fn0.size() * 8),
-           i_fsys = add(c->fn_sys.data(), c->fn_sys.size() * 4), i_status = add(nullptr, 64);
+           i_fsys = add(c->fn_sys.data(), c->fn_sys.size() * 4), i_status = add(nullptr, 64),
+           i_snnz = add(sys_nnz.data(), sys_nnz.size() * 8), i_colg = add(col_glob.data(), col_glob.size() * 4);
     cudaError_t e = cudaMalloc((void **)&c->d_arena, total);
     if (e != cudaSuccess) {
         c->d_arena = nullptr;
@@ -493,6 +509,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     c->d_sys_val0 = (long long *)at(i_sv0);
     c->d_sys_fn0 = (long long *)at(i_sf0);
     c->d_fn_sys = (int *)at(i_fsys);
+    c->d_sys_nnz = (long long *)at(i_snnz);
+    P.col_glob = (const int *)at(i_colg);
     c->d_status = (int *)at(i_status);
 
     // tensor-core path plan (operand images, tiles, waves)
@@ -503,6 +521,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     tin.atom_nfn = c->atom_nfn.data();
     tin.tune_path = tune_path;
     tin.nnz = c->nnz;
+    tin.n_fn = c->n_fn;
     std::string terr;
     int rc = tc_build(c->tc, tin, &terr);
     if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
@@ -889,7 +908,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
         const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
         {
             ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz);
-            CUDA_TRY(c, tc_launch_to_df(d, ws, c->nnz, s));
+            CUDA_TRY(c, tc_launch_to_df(c->tc, P, d, ws, c->d_sys_val0, c->d_sys_nnz, c->d_fn_sys, s));
         }
         for (const TcWave &w : c->tc.waves) {
             {
@@ -898,7 +917,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
             }
             {
                 ProfScope ps(c, s, 4, 0.0, w.g_bytes);
-                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, ws, 1.0, ws, n_split, s));
+                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, 1.0, ws, n_split, s));
             }
             ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
             CUDA_TRY(c, tc_launch_density(c->tc, P, w, ws, n, n_split, s));

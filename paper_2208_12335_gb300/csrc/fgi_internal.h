@@ -75,6 +75,7 @@ struct DevPlan {
     const long long *sys_pair_off;// offset of the system's pairpos table
     const int *pairpos;           // [nat*nat] per system: position of atom b's run in atom a's row, -1 absent
     const long long *rowptr;      // per global function: index of its first stored value
+    const int *col_glob;          // per stored value: global column function, -1 on the diagonal
     // batches
     const DevBatch *batches;
     const DevAct *act;

@@ -77,13 +77,18 @@ __device__ __forceinline__ uint64_t global_ns()
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a wait that long means a bug
 
-// Bounded wait on an mbarrier phase; on time-out records kStatusTimeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+// Bounded wait on an mbarrier phase (time-out: kStatusTimeout), with a CTA-wide abort flag: once any wait of the CTA has
+// timed out, every later wait fails at once, so that the roles finish their
+// loops quickly with unchanged control flow (no named barrier is skipped).
+__device__ __forceinline__ bool mbar_wait_a(uint64_t *bar, uint32_t parity, int *status, volatile int *abort)
 {
     if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
         if (global_ns() - t0 > kWaitLimitNs) {
+            *abort = 1;
             atomicOr(status, kStatusTimeout);
             return false;
         }
@@ -378,7 +383,12 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
         const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
         const df d = df_sqrt(df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z)));
         const bool origin = d.hi < 1e-12f;
-        const df inv = origin ? df{0.f, 0.f} : df_rcp(d);
+        // 1/d^(l+1), l = 0..3, as double-floats
+        df ipow[4];
+        ipow[0] = origin ? df{0.f, 0.f} : df_rcp(d);
+        ipow[1] = df_mul(ipow[0], ipow[0]);
+        ipow[2] = df_mul(ipow[1], ipow[0]);
+        ipow[3] = df_mul(ipow[2], ipow[0]);
         int f = 0;
         for (int sh = 0; sh < S.n_shell; sh++) {
             const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
@@ -395,27 +405,35 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                         rad = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});
                     }
                 } else {
+                    // t = frac(d/h) from the double-float d; u = c0 + t (c1 + t (c2 + t c3))
+                    // with c0 in double-float and the (smaller) polynomial tail in FP32
                     const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
                     int kk = (int)floorf(s.hi);
                     kk = max(0, min(kk, R.nk - 2));
-                    const df t = df_two_sum(s.hi - (float)kk, s.lo);
+                    const float t = (s.hi - (float)kk) + s.lo;
                     const float4 ch = __ldg(P.coef_dd + 2 * (R.coef_off + kk));
-                    const float4 cl = __ldg(P.coef_dd + 2 * (R.coef_off + kk) + 1);
-                    df uu{ch.w, cl.w};
-                    uu = df_add(df_mul(uu, t), df{ch.z, cl.z});
-                    uu = df_add(df_mul(uu, t), df{ch.y, cl.y});
-                    uu = df_add(df_mul(uu, t), df{ch.x, cl.x});
-                    rad = df_mul(uu, inv);
-                    for (int q = 0; q < R.l; q++) rad = df_mul(rad, inv);
+                    const float c0lo = __ldg(reinterpret_cast<const float *>(P.coef_dd + 2 * (R.coef_off + kk) + 1));
+                    const float tail = t * (ch.y + t * (ch.z + t * ch.w));
+                    df uu = df_two_sum(ch.x, tail);
+                    uu = df_fast_two_sum(uu.hi, uu.lo + c0lo);
+                    rad = df_mul(uu, ipow[R.l]);
                 }
             }
             float Q[7];
             int ci[7];
             ylm_poly_f32(R.l, x.hi, y.hi, z.hi, Q, ci);
+            // radial factor times each distinct normalisation constant of the shell
+            df rc[5];
+            const int cbase = ci[0];
+            const int ncst = R.l < 2 ? 1 : (R.l == 2 ? 3 : 5);
+            for (int q = 0; q < ncst; q++) {
+                const float2 cc = kYlmC[R.l == 2 ? 2 + q : (R.l == 3 ? 5 + q : cbase)];
+                rc[q] = df_mul(rad, df{cc.x, cc.y});
+            }
             for (int m = 0; m < nm; m++, f++) {
                 if (f < f_lo || f >= f_hi) continue;
-                const float2 cc = kYlmC[ci[m]];
-                const df val = df_mul_f(df_mul(rad, df{cc.x, cc.y}), Q[m]);
+                const int qi = R.l < 2 ? 0 : (R.l == 2 ? ci[m] - 2 : ci[m] - 5);
+                const df val = df_mul_f(rc[qi], Q[m]);
                 out[f * kPhiValStride] = make_float2(val.hi, val.lo);
             }
         }
@@ -668,21 +686,12 @@ __device__ __forceinline__ long long f32_to_fix(float f, bool &bad)
 {
     const unsigned u = __float_as_uint(f);
     const int e = (int)((u >> 23) & 0xFFu);
-    if (e == 0) return 0;                                   // zero or below 1.2e-38
     const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
     const int sh = e - 150 + kFixBits;                      // f = m 2^(e-150)
-    long long r;
-    if (sh > 38) {
-        bad = true;
-        r = 0;
-    } else if (sh >= 0) {
-        r = m << sh;
-    } else if (sh > -25) {
-        r = (m + (1ll << (-sh - 1))) >> -sh;
-    } else {
-        r = 0;
-    }
-    return (u >> 31) ? -r : r;
+    bad |= sh > 38;
+    long long r = sh >= 0 ? (m << min(sh, 38)) : (m >> min(-sh, 63));   // truncation below 2^-40
+    r = e == 0 ? 0 : r;                                     // zero or below 1.2e-38
+    return (int)u < 0 ? -r : r;
 }
 
 // h[k] = (accumulate ? h[k] : 0) + acc[k] 2^-40
@@ -695,45 +704,90 @@ __global__ void k_fix_to_h(const long long *acc, double *h, long long n, int acc
 }
 
 // ----------------------------------------------- H contraction on tcgen05 (K2)
-// CTA per tile (batch, I, J), I <= J: 128 x 128 outputs, K = points in
-// chunks of 64.  Warp 4: bulk-copy producer; warp 5: MMA issuer; warps 0-3:
-// epilogue (TMEM lanes 32w..32w+31), FP64 atomic scatter of the upper triangle.
-constexpr int kThreadsTc = 192;
+// Persistent: one CTA per SM walks the tile list (batch, I, J), I <= J, with
+// stride gridDim.x; each tile is 128 x 128 outputs with K = the batch's
+// points in chunks of 64.  Warp 4 (one lane) streams operand chunks into a
+// two-stage shared-memory ring with bulk copies; warp 5 (one lane) issues
+// the MMAs into one of two tensor-memory accumulator sets (acc0 + acc1,
+// 256 columns each); warps 0-3 drain the other set (TMEM lanes 32w..32w+31)
+// and scatter the upper triangle into the fixed-point H accumulator, so the
+// scatter of one tile overlaps the MMAs of the next.
+constexpr int kThreadsTc = 320;                  // warps 0-7 epilogue, 8 producer, 9 MMA
+constexpr int kWarpProducer = 8, kWarpMma = 9;
+constexpr int kEpiThreads = 256;
+constexpr int kStages = 2;
+constexpr int kStageBytes = 6 * kChunkBytes;     // A and B operands, 3 planes each
 
-struct TcSmem {
-    uint64_t full, empty, done, acc_empty;
-    uint32_t tmem;
-    int pad[7];
-    FnRef ref[128];
+struct ColRef {                                  // compact column reference for the H scatter
+    int gi;                                      // global function
+    int atom;                                    // global atom
+    int li;                                      // index inside the atom
+    int loc;                                     // atom index inside its system
 };
 
-__global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                        const uint8_t *ws, unsigned long long *hfix, int n_split)
+struct TcRing {
+    uint64_t full[kStages], empty[kStages];
+    uint64_t tfull[2], tempty[2];
+    uint32_t tmem;
+    int abort;
+    int pad[2];
+    ColRef ref[2][128];
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p)
+{
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+// named barrier of the eight epilogue warps
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void ring_init(TcRing *S)
+{
+    for (int s = 0; s < kStages; s++) {
+        mbar_init(&S->full[s], 1);
+        mbar_init(&S->empty[s], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+        mbar_init(&S->tfull[b], 1);
+        mbar_init(&S->tempty[b], kEpiThreads);
+    }
+    S->abort = 0;
+    fence_mbar_init();
+}
+
+// issue the split products of one 64-deep chunk (4 k-steps of 16)
+__device__ __forceinline__ void mma_chunk(uint32_t acc_base, const uint8_t *a_sm, const uint8_t *b_sm, uint32_t idesc,
+                                         int n_split, bool b_mn, bool *started)
+{
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        for (int pa = 0; pa < n_split; pa++) {
+            for (int pb = 0; pb < n_split; pb++) {
+                // split: every product but x2*y2 (x0*y0 alone in accumulator 0)
+                if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
+                const int acc = (pa + pb == 0) ? 0 : 1;
+                const uint64_t ad = desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
+                const uint64_t bd = b_mn ? desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 2048), 8192, 1024)
+                                         : desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 32), 16, 1024);
+                tc_mma(acc_base + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
+                started[acc] = true;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                        int n_items, const uint8_t *ws, unsigned long long *hfix,
+                                                        int n_split)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *a_sm = sm;
-    uint8_t *b_sm = sm + n_split * kChunkBytes;
-    TcSmem *S = reinterpret_cast<TcSmem *>(sm + 2 * n_split * kChunkBytes);
-
-    const WorkItem it = items[blockIdx.x];
-    const DevBatch B = P.batches[it.batch];
-    const TcBatch T = tb[it.batch];
+    uint8_t *sm = align1024(smem_raw);
+    TcRing *S = reinterpret_cast<TcRing *>(sm + kStages * kStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const DevAct *act = P.act + B.act0;
-    const int i0 = it.ti * 128, j0 = it.tj * 128;
-    if (threadIdx.x < 128 && j0 + (int)threadIdx.x < B.nfn) {
-        const int j = j0 + threadIdx.x;
-        S->ref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, j), j);
-    }
-    if (threadIdx.x == 0) {
-        mbar_init(&S->full, 1);
-        mbar_init(&S->empty, 1);
-        mbar_init(&S->done, 1);
-        fence_mbar_init();
-    }
-    if (warp == 5) {
-        tmem_alloc(&S->tmem, 256);
+    if (threadIdx.x == 0) ring_init(S);
+    if (warp == kWarpMma) {
+        tmem_alloc(&S->tmem, 512);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -741,94 +795,140 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_h(DevPlan P, const TcBatch
     tc_fence_after();
     const uint32_t tmem = S->tmem;
     const uint32_t chunk = (uint32_t)n_split * kChunkBytes;
-    const uint8_t *a_img = ws + T.img_aux;
-    const uint8_t *b_img = ws + T.img_phi;
-    const int nc = T.nc;
 
-    if (warp == 4) {
+    if (warp == kWarpProducer) {
         if (lane == 0) {
-            for (int c = 0; c < nc; c++) {
-                if (c > 0 && !mbar_wait(&S->empty, (c - 1) & 1, P.status)) break;
-                mbar_expect_tx(&S->full, 2 * chunk);
-                for (int s = 0; s < n_split; s++) {
-                    bulk_g2s(a_sm + s * kChunkBytes,
-                             a_img + s * T.plane_phi + (long long)(it.ti * T.nc_alloc + c) * kChunkBytes,
-                             kChunkBytes, &S->full);
-                    bulk_g2s(b_sm + s * kChunkBytes,
-                             b_img + s * T.plane_phi + (long long)(it.tj * T.nc_alloc + c) * kChunkBytes,
-                             kChunkBytes, &S->full);
+            long long n = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+                const WorkItem it = items[t];
+                const TcBatch T = tb[it.batch];
+                const uint8_t *a_img = ws + T.img_aux, *b_img = ws + T.img_phi;
+                for (int c = 0; c < T.nc; c++, n++) {
+                    const int st = (int)(n % kStages);
+                    const long long use = n / kStages;
+                    if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *a_sm = sm + st * kStageBytes, *b_sm = a_sm + 3 * kChunkBytes;
+                    mbar_expect_tx(&S->full[st], 2 * chunk);
+                    for (int s = 0; s < n_split; s++) {
+                        bulk_g2s(a_sm + s * kChunkBytes,
+                                 a_img + s * T.plane_phi + (long long)(it.ti * T.nc_alloc + c) * kChunkBytes,
+                                 kChunkBytes, &S->full[st]);
+                        bulk_g2s(b_sm + s * kChunkBytes,
+                                 b_img + s * T.plane_phi + (long long)(it.tj * T.nc_alloc + c) * kChunkBytes,
+                                 kChunkBytes, &S->full[st]);
+                    }
                 }
             }
             // do not leave while a copy may still be landing
-            mbar_wait(&S->empty, (nc - 1) & 1, P.status);
+            for (long long q = (n > kStages ? n - kStages : 0); q < n; q++)
+                mbar_wait_a(&S->empty[q % kStages], (uint32_t)((q / kStages) & 1), P.status, &S->abort);
         }
-    } else if (warp == 5) {
+        __syncwarp();
+    } else if (warp == kWarpMma) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(128, 128, false, false);
-            bool started[2] = {false, false};
+            long long n = 0;
+            int lt = 0;
             bool ok = true;
-            for (int c = 0; c < nc && ok; c++) {
-                if (!mbar_wait(&S->full, c & 1, P.status)) {
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x, lt++) {
+                const TcBatch T = tb[items[t].batch];
+                const int buf = lt & 1, use = lt >> 1;
+                if (use > 0 && !mbar_wait_a(&S->tempty[buf], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                bool started[2] = {false, false};
+                for (int c = 0; c < T.nc; c++, n++) {
+                    const int st = (int)(n % kStages);
+                    if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint8_t *a_sm = sm + st * kStageBytes;
+                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, false, started);
+                    tc_commit(&S->empty[st]);
+                }
+                tc_commit(&S->tfull[buf]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 64 (w / 4) .. + 63
+        int lt = 0;
+        bool bad = false;
+        const int quad = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        for (int t = blockIdx.x; t < n_items; t += gridDim.x, lt++) {
+            const WorkItem it = items[t];
+            const DevBatch B = P.batches[it.batch];
+            const DevAct *act = P.act + B.act0;
+            const int buf = lt & 1, use = lt >> 1;
+            const int i0 = it.ti * 128, j0 = it.tj * 128;
+            if (threadIdx.x < 128) {
+                const int j = j0 + threadIdx.x;
+                if (j < B.nfn) {
+                    const FnRef c = fn_ref(P, act, find_act(act, B.n_act, j), j);
+                    S->ref[buf][threadIdx.x] = ColRef{(int)c.gi, c.atom, c.li, c.loc};
+                }
+            }
+            const int r = quad * 32 + lane;
+            const int i = i0 + r;
+            FnRef rref{};
+            if (i < B.nfn) rref = fn_ref(P, act, find_act(act, B.n_act, i), i);
+            const int *pp_row = P.pairpos + P.sys_pair_off[B.sys] + (long long)rref.loc * P.sys_nat[B.sys];
+            epi_sync();
+            const bool ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
+            tc_fence_after();
+            const uint32_t acc_base = tmem + buf * 256 + lane_base;
+            for (int cq = 0; cq < 2; cq++) {
+                const int cc = 2 * half + cq;
+                if (j0 + cc * 32 >= B.nfn) break;
+                float a0[32], a1[32];
+                tmem_ld32(acc_base + cc * 32, a0);
+                if (n_split > 1) tmem_ld32(acc_base + 128 + cc * 32, a1);
+                tmem_wait_ld();
+                if (!ok || i >= B.nfn) continue;
+                // stored value of (i, j) = base(atom of j) + gj along a run of one atom
+                int cur_atom = -1;
+                long long base = 0;           // may be negative: k = base + gj
+                bool stored = false;
 #pragma unroll
-                for (int ks = 0; ks < 4; ks++) {
-                    for (int pa = 0; pa < n_split; pa++) {
-                        for (int pb = 0; pb < n_split; pb++) {
-                            // split: every product but x2*y2 (x0*y0 alone in accumulator 0)
-                            if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
-                            const int acc = (pa + pb == 0) ? 0 : 1;
-                            const uint64_t ad = desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
-                            const uint64_t bd = desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 32), 16, 1024);
-                            tc_mma(tmem + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
-                            started[acc] = true;
+                for (int q = 0; q < 32; q++) {
+                    const int jl = cc * 32 + q;
+                    const int j = j0 + jl;
+                    if (j >= B.nfn || i > j) continue;
+                    const ColRef cj = S->ref[buf][jl];
+                    if (cj.atom != cur_atom) {
+                        cur_atom = cj.atom;
+                        if (cj.atom == rref.atom) {
+                            base = rref.rp - rref.gi;
+                            stored = true;
+                        } else {
+                            const int pp = __ldg(pp_row + cj.loc);
+                            stored = pp >= 0;
+                            base = rref.rp + pp - rref.li - (cj.gi - cj.li);
                         }
                     }
+                    if (!stored) continue;
+                    long long fx = f32_to_fix(a0[q], bad);
+                    if (n_split > 1) fx += f32_to_fix(a1[q], bad);
+                    if (fx != 0) atomicAdd(hfix + base + cj.gi, (unsigned long long)fx);
                 }
-                tc_commit(&S->empty);
             }
-            tc_commit(&S->done);
-        }
-    }
-    __syncwarp();
-
-    if (warp < 4) {
-        const bool ok = mbar_wait(&S->done, 0, P.status);
-        tc_fence_after();
-        const int r = warp * 32 + lane;
-        const int i = i0 + r;
-        const bool row_ok = ok && i < B.nfn;
-        FnRef rref{};
-        if (row_ok) rref = fn_ref(P, act, find_act(act, B.n_act, i), i);
-        const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
-        const int nat = P.sys_nat[B.sys];
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        bool bad = false;
-        for (int cc = 0; cc < 4; cc++) {
-            if (j0 + cc * 32 >= B.nfn) break;
-            float a0[32], a1[32];
-            tmem_ld32(tmem + lane_base + cc * 32, a0);
-            if (n_split > 1) tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
-            tmem_wait_ld();
-            if (!row_ok) continue;
-#pragma unroll
-            for (int q = 0; q < 32; q++) {
-                const int jl = cc * 32 + q;
-                const int j = j0 + jl;
-                if (j >= B.nfn || i > j) continue;
-                long long fx = f32_to_fix(a0[q], bad);
-                if (n_split > 1) fx += f32_to_fix(a1[q], bad);
-                const long long k = value_index_pp(pp_sys, nat, rref, S->ref[jl]);
-                if (k >= 0 && fx != 0) atomicAdd(hfix + k, (unsigned long long)fx);
-            }
+            tc_fence_before();
+            mbar_arrive(&S->tempty[buf]);
         }
         if (bad) atomicOr(P.status, kStatusNonFinite);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) tmem_dealloc(tmem, 256);
+    if (warp == kWarpMma) tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------- D_b gather (K3a)
@@ -850,26 +950,62 @@ __device__ __forceinline__ df gather_d_value(const int *pp_sys, int nat, int nfn
     return df{v.x * sc, v.y * sc};
 }
 
-// D values as double-floats (once per density call; nnz elements)
-__global__ void k_to_df(const double *x, float2 *out, long long n)
+// D values as double-floats (once per density call; nnz elements), and for
+// every function g the largest |D_gi| and the sum of |D_gi| over its full
+// symmetric row: bounds (valid for every batch) for the fixed-point grid of
+// the gathered rows.  One warp per row of the stored upper triangle.
+__global__ void k_to_df(const double *x, float2 *out, const long long *rowptr, const int *fn_sys,
+                        const long long *sys_val0, const long long *sys_nnz, long long n_fn, unsigned int *gmax,
+                        float *gsum)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const df v = df_from_double(x[k]);
-        out[k] = make_float2(v.hi, v.lo);
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = warp0; g < n_fn; g += nwarps) {
+        const int s = fn_sys[g];
+        const long long k0 = rowptr[g];
+        const long long k1 = (g + 1 < n_fn && fn_sys[g + 1] == s) ? rowptr[g + 1] : sys_val0[s] + sys_nnz[s];
+        float mx = 0.f, sm = 0.f;
+        for (long long k = k0 + lane; k < k1; k += 32) {
+            const df v = df_from_double(x[k]);
+            out[k] = make_float2(v.hi, v.lo);
+            float a = fabsf(v.hi);
+            if (!(a < 1.0e30f)) a = 1.0e30f;
+            mx = fmaxf(mx, a);
+            sm += a;
+        }
+        mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        if (lane == 0) {
+            atomicMax(gmax + g, __float_as_uint(mx));
+            atomicAdd(gsum + g, sm);
+        }
+    }
+}
+
+// the column side of the symmetric rows: value (g, j), j > g, bounds row j
+__global__ void k_d_colbounds(const float2 *v, const int *col_of, long long nnz, unsigned int *gmax, float *gsum)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+        const int j = col_of[k];
+        if (j < 0) continue;                       // diagonal entries are counted once
+        float a = fabsf(v[k].x);
+        if (!(a < 1.0e30f)) a = 1.0e30f;
+        atomicMax(gmax + j, __float_as_uint(a));
+        atomicAdd(gsum + j, a);
     }
 }
 
 __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                     uint8_t *ws, const float2 *ddv, float offdiag_scale,
-                                                     int n_split)
+                                                     uint8_t *ws, const float2 *ddv, const unsigned int *gmax,
+                                                     const float *gsum, float offdiag_scale, int n_split)
 {
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
     const TcBatch T = tb[it.batch];
     const int J = it.ti;
     __shared__ FnRef rref[128], cref[64];
-    __shared__ unsigned int rowmax[128];
-    __shared__ float rowsum[128];
     __shared__ float rsc[2][128];
     const DevAct *act = P.act + B.act0;
     const bool fixed = n_split == 3;
@@ -877,91 +1013,61 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
     const int nat = P.sys_nat[B.sys];
     if (threadIdx.x < 128) {
         const int j = J * 128 + threadIdx.x;
-        if (j < B.nfn) rref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, j), j);
-        rowmax[threadIdx.x] = 0u;
-        rowsum[threadIdx.x] = 0.f;
+        float sc = 0.f, un = 0.f;
+        if (j < B.nfn) {
+            const FnRef rj = fn_ref(P, act, find_act(act, B.n_act, j), j);
+            rref[threadIdx.x] = rj;
+            if (fixed) fixed_scale_adaptive(__uint_as_float(gmax[rj.gi]), gsum[rj.gi], T.nkc * 64, sc, un);
+        }
+        rsc[0][threadIdx.x] = sc;
+        rsc[1][threadIdx.x] = un;
     }
     uint8_t *img = ws + T.img_aux;
-    for (int pass = fixed ? 0 : 1; pass < 2; pass++) {
-        if (pass == 1 && fixed) {
-            __syncthreads();
-            if (threadIdx.x < 128) {
-                float sc, un;
-                fixed_scale_adaptive(__uint_as_float(rowmax[threadIdx.x]), rowsum[threadIdx.x], T.nkc * 64, sc, un);
-                rsc[0][threadIdx.x] = sc;
-                rsc[1][threadIdx.x] = un;
-            }
+    for (int kc = 0; kc < T.nkc; kc++) {
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int i = kc * 64 + threadIdx.x;
+            if (i < B.nfn) cref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, i), i);
         }
-        for (int kc = 0; kc < T.nkc; kc++) {
-            __syncthreads();
-            if (threadIdx.x < 64) {
-                const int i = kc * 64 + threadIdx.x;
-                if (i < B.nfn) cref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, i), i);
-            }
-            __syncthreads();
-            for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
-                const int r = u >> 3, g = u & 7;
-                const int j = J * 128 + r;
-                df x[8];
+        __syncthreads();
+        for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
+            const int r = u >> 3, g = u & 7;
+            const int j = J * 128 + r;
+            df x[8];
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int il = g * 8 + q;
-                    x[q] = gather_d_value(pp_sys, nat, B.nfn, rref[r], cref[il], j, kc * 64 + il, ddv, offdiag_scale);
-                }
-                if (pass == 0) {
-                    float mx = 0.f, sm = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        mx = fmaxf(mx, fabsf(x[q].hi));
-                        sm += fabsf(x[q].hi);
-                    }
-                    if (!(mx < 1.0e30f)) mx = 1.0e30f;
-                    if (!(sm < 1.0e30f)) sm = 1.0e30f;
-                    atomicMax(&rowmax[r], __float_as_uint(mx));
-                    atomicAdd(&rowsum[r], sm);
-                    continue;
-                }
-                uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
-                if (fixed)
-                    store_fixed8(dst, T.plane_d, x, rsc[0][r], rsc[1][r]);
-                else
-                    store_split8_df(dst, T.plane_d, x, n_split);
+            for (int q = 0; q < 8; q++) {
+                const int il = g * 8 + q;
+                x[q] = gather_d_value(pp_sys, nat, B.nfn, rref[r], cref[il], j, kc * 64 + il, ddv, offdiag_scale);
             }
+            uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
+            if (fixed)
+                store_fixed8(dst, T.plane_d, x, rsc[0][r], rsc[1][r]);
+            else
+                store_split8_df(dst, T.plane_d, x, n_split);
         }
     }
 }
 
 // ------------------------------------------------- density on tcgen05 (K3b)
-// CTA per (batch, 128-point tile m).  For each 128-function block J:
-// E^T[j][p] = sum_i D[j][i] phi_i(p) (A = D image, K-major; B = phi image
-// read as MN-major), then n_p += sum_j E^T[j][p] phi_j(p) in FP64: lane j
-// multiplies by its own phi row and the warp reduces over j.
-__global__ void __launch_bounds__(kThreadsTc, 2) k_tc_density(DevPlan P, const TcBatch *tb,
-                                                              const WorkItem *items, const uint8_t *ws,
-                                                              double *n_out, int n_split)
+// Persistent: one CTA per SM walks the items (batch, 128-point tile m); for
+// each 128-function block J of the batch, E^T[j][p] = sum_i D[j][i] phi_i(p)
+// (A = D image, K-major; B = phi image read as MN-major) accumulates in one
+// of two tensor-memory sets while warps 0-3 finish the previous block:
+// n_p += sum_j E^T[j][p] phi_j(p) in double-float, lane j multiplying by its
+// own phi row and the warp reducing over j.
+__global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                              int n_items, const uint8_t *ws, double *n_out,
+                                                              int n_split)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *a_sm = sm;                              // D chunk: n_split x 16 KB
-    uint8_t *b_sm = sm + n_split * kChunkBytes;      // phi chunk: n_split x (2 x 8 KB)
-    TcSmem *S = reinterpret_cast<TcSmem *>(sm + 2 * n_split * kChunkBytes);
+    uint8_t *sm = align1024(smem_raw);
+    TcRing *S = reinterpret_cast<TcRing *>(sm + kStages * kStageBytes);
     __shared__ double red[4][128];
-
-    const WorkItem it = items[blockIdx.x];
-    const DevBatch B = P.batches[it.batch];
-    const TcBatch T = tb[it.batch];
-    const int m = it.ti;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = threadIdx.x; k < 512; k += blockDim.x) (&red[0][0])[k] = 0.0;
-    if (threadIdx.x == 0) {
-        mbar_init(&S->full, 1);
-        mbar_init(&S->empty, 1);
-        mbar_init(&S->done, 1);
-        mbar_init(&S->acc_empty, 128);
-        fence_mbar_init();
-    }
-    if (warp == 5) {
-        tmem_alloc(&S->tmem, 256);
+    if (threadIdx.x == 0) ring_init(S);
+    if (warp == kWarpMma) {
+        tmem_alloc(&S->tmem, 512);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -969,97 +1075,110 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_density(DevPlan P, const T
     tc_fence_after();
     const uint32_t tmem = S->tmem;
     const uint32_t chunk = (uint32_t)n_split * kChunkBytes;
-    const uint8_t *d_img = ws + T.img_aux;
-    const uint8_t *phi_img = ws + T.img_phi;
-    const int nkc = T.nkc, nrb = T.nrb;
 
-    if (warp == 4) {
+    if (warp == kWarpProducer) {
         if (lane == 0) {
-            int n = 0;
+            long long n = 0;
             bool ok = true;
-            for (int J = 0; J < nrb && ok; J++) {
-                for (int kc = 0; kc < nkc; kc++, n++) {
-                    if (n > 0 && !mbar_wait(&S->empty, (n - 1) & 1, P.status)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&S->full, 2 * chunk);
-                    const int I = kc >> 1, half = kc & 1;
-                    for (int s = 0; s < n_split; s++) {
-                        bulk_g2s(a_sm + s * kChunkBytes,
-                                 d_img + s * T.plane_d + (long long)(J * nkc + kc) * kChunkBytes, kChunkBytes,
-                                 &S->full);
-                        for (int c2 = 0; c2 < 2; c2++)
-                            bulk_g2s(b_sm + s * kChunkBytes + c2 * 8192,
-                                     phi_img + s * T.plane_phi +
-                                         ((long long)(I * T.nc_alloc + 2 * m + c2) * 16 + 8 * half) * 1024,
-                                     8192, &S->full);
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+                const WorkItem it = items[t];
+                const TcBatch T = tb[it.batch];
+                const int m = it.ti;
+                const uint8_t *d_img = ws + T.img_aux, *phi_img = ws + T.img_phi;
+                for (int J = 0; J < T.nrb && ok; J++) {
+                    for (int kc = 0; kc < T.nkc; kc++, n++) {
+                        const int st = (int)(n % kStages);
+                        const long long use = n / kStages;
+                        if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *a_sm = sm + st * kStageBytes, *b_sm = a_sm + 3 * kChunkBytes;
+                        mbar_expect_tx(&S->full[st], 2 * chunk);
+                        const int I = kc >> 1, half = kc & 1;
+                        for (int s = 0; s < n_split; s++) {
+                            bulk_g2s(a_sm + s * kChunkBytes,
+                                     d_img + s * T.plane_d + (long long)(J * T.nkc + kc) * kChunkBytes, kChunkBytes,
+                                     &S->full[st]);
+                            for (int c2 = 0; c2 < 2; c2++)
+                                bulk_g2s(b_sm + s * kChunkBytes + c2 * 8192,
+                                         phi_img + s * T.plane_phi +
+                                             ((long long)(I * T.nc_alloc + 2 * m + c2) * 16 + 8 * half) * 1024,
+                                         8192, &S->full[st]);
+                        }
                     }
                 }
             }
-            if (ok && n > 0) mbar_wait(&S->empty, (n - 1) & 1, P.status);
+            for (long long q = (n > kStages ? n - kStages : 0); q < n; q++)
+                mbar_wait_a(&S->empty[q % kStages], (uint32_t)((q / kStages) & 1), P.status, &S->abort);
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == kWarpMma) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(128, 128, false, true);
-            int n = 0;
+            long long n = 0;
+            int u = 0;
             bool ok = true;
-            for (int J = 0; J < nrb && ok; J++) {
-                if (J > 0 && !mbar_wait(&S->acc_empty, (J - 1) & 1, P.status)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                bool started[2] = {false, false};
-                for (int kc = 0; kc < nkc; kc++, n++) {
-                    if (!mbar_wait(&S->full, n & 1, P.status)) {
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
+                const TcBatch T = tb[items[t].batch];
+                for (int J = 0; J < T.nrb && ok; J++, u++) {
+                    const int buf = u & 1, use = u >> 1;
+                    if (use > 0 && !mbar_wait_a(&S->tempty[buf], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-#pragma unroll
-                    for (int ks = 0; ks < 4; ks++) {
-                        for (int pa = 0; pa < n_split; pa++) {
-                            for (int pb = 0; pb < n_split; pb++) {
-                                if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
-                                const int acc = (pa + pb == 0) ? 0 : 1;
-                                const uint64_t ad =
-                                    desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
-                                const uint64_t bd =
-                                    desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 2048), 8192, 1024);
-                                tc_mma(tmem + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
-                                started[acc] = true;
-                            }
+                    bool started[2] = {false, false};
+                    for (int kc = 0; kc < T.nkc; kc++, n++) {
+                        const int st = (int)(n % kStages);
+                        if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint8_t *a_sm = sm + st * kStageBytes;
+                        mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started);
+                        tc_commit(&S->empty[st]);
                     }
-                    tc_commit(&S->empty);
+                    tc_commit(&S->tfull[buf]);
                 }
-                tc_commit(&S->done);     // accumulator of block J complete
             }
         }
         __syncwarp();
     } else {
-        // epilogue warps 0-3: row j = J*128 + 32*warp + lane
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int J = 0; J < nrb; J++) {
-            const bool ok = mbar_wait(&S->done, J & 1, P.status);
-            tc_fence_after();
-            const int r = warp * 32 + lane;
-            const int j = J * 128 + r;
-            for (int cc = 0; cc < 4; cc++) {
-                float a0[32], a1[32];
-                tmem_ld32(tmem + lane_base + cc * 32, a0);
-                if (n_split > 1)
-                    tmem_ld32(tmem + lane_base + 128 + cc * 32, a1);
-                else
+        // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (functions j of the
+        // block), point columns 64 (w / 4) .. + 63
+        const int quad = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        int u = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
+            const WorkItem it = items[t];
+            const DevBatch B = P.batches[it.batch];
+            const TcBatch T = tb[it.batch];
+            const int m = it.ti;
+            const uint8_t *phi_img = ws + T.img_phi;
+            for (int J = 0; J < T.nrb; J++, u++) {
+                const int buf = u & 1, use = u >> 1;
+                ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
+                tc_fence_after();
+                const int r = quad * 32 + lane;
+                const int j = J * 128 + r;
+                const uint32_t acc_base = tmem + buf * 256 + lane_base;
+                for (int cq = 0; cq < 2; cq++) {
+                    const int cc = 2 * half + cq;
+                    float a0[32], a1[32];
+                    tmem_ld32(acc_base + cc * 32, a0);
+                    if (n_split > 1)
+                        tmem_ld32(acc_base + 128 + cc * 32, a1);
+                    else
 #pragma unroll
-                    for (int q = 0; q < 32; q++) a1[q] = 0.f;
-                tmem_wait_ld();
-                if (cc == 3) {
-                    tc_fence_before();
-                    mbar_arrive(&S->acc_empty);   // accumulator may be overwritten
-                }
+                        for (int q = 0; q < 32; q++) a1[q] = 0.f;
+                    tmem_wait_ld();
+                    if (cq == 1) {
+                        tc_fence_before();
+                        mbar_arrive(&S->tempty[buf]);     // accumulator set may be reused
+                    }
                 // E^T[j][p] phi_j(p) for the 32 points of this column chunk in
                 // double-float (FP32 pipe): e = acc0 + acc1, phi = sum of its planes
                 const int c = 2 * m + (cc >> 1);
@@ -1101,24 +1220,33 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_tc_density(DevPlan P, const T
                         a1[q] = sum.lo;
                     }
                 }
-                red[warp][cc * 32 + lane] += (double)a0[0] + (double)a1[0];
+                    red[quad][cc * 32 + lane] += (double)a0[0] + (double)a1[0];
+                }
             }
+            // item complete: n_p from the four warps' partial sums
+            epi_sync();
+            if (threadIdx.x < 128) {
+                const int p = m * 128 + threadIdx.x;
+                if (ok && p < B.np)
+                    n_out[B.pt0 + p] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
+                                       red[3][threadIdx.x];
+            }
+            epi_sync();
+            for (int cq = 0; cq < 2; cq++) red[quad][(2 * half + cq) * 32 + lane] = 0.0;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x < 128) {
-        const int p = m * 128 + threadIdx.x;
-        if (p < B.np)
-            n_out[B.pt0 + p] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
-    }
-    if (warp == 5) tmem_dealloc(tmem, 256);
+    if (warp == kWarpMma) tmem_dealloc(tmem, 512);
 }
 
-// Dynamic shared memory of the tcgen05 kernels.  Launches always use the
-// 3-plane size so that at most two CTAs share an SM: each holds 256 of the
-// SM's 512 tensor-memory columns.
-size_t smem_tc(int n_split) { return 1024 + 2 * (size_t)n_split * kChunkBytes + sizeof(TcSmem); }
+// Dynamic shared memory of the tcgen05 kernels: the two-stage ring (about
+// 200 KB) keeps one CTA per SM, which holds all 512 tensor-memory columns.
+size_t smem_tc(int n_split)
+{
+    (void)n_split;
+    return 1024 + (size_t)kStages * kStageBytes + sizeof(TcRing);
+}
 
 size_t smem_phi() { return 128 * kPhiValStride * sizeof(float2); }
 
@@ -1226,9 +1354,12 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
             wv.g_bytes += 8.0 * n * n + 6.0 * n * n;
         }
     }
-    // scratch before the images: the fixed-point H accumulator or the
-    // double-float copy of D (nnz x 8 bytes either way)
-    t.img_base = ((size_t)in.nnz * 8 + 1023) / 1024 * 1024;
+    // scratch before the images: the fixed-point H accumulator, or the
+    // double-float copy of D followed by the per-function bounds of D
+    t.nnz = in.nnz;
+    t.n_fn = in.n_fn;
+    t.bound_off = ((size_t)in.nnz * 8 + 255) / 256 * 256;
+    t.img_base = (t.bound_off + 8 * (size_t)in.n_fn + 1023) / 1024 * 1024;
     t.ws_bytes = t.img_base + max_ws + 1024;
     // items must not be empty for the device copy
     if (!in.host_only) {
@@ -1247,6 +1378,10 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         if (ni_bytes) cudaMemcpy(base + ioff, t.items.data(), ni_bytes, cudaMemcpyHostToDevice);
         t.d_batches = (const TcBatch *)base;
         t.d_items = (const WorkItem *)(base + ioff);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (t.num_sms <= 0) t.num_sms = 1;
         e = set_attrs();
         if (e != cudaSuccess) {
             *err = std::string("tensor-core plan: cudaFuncSetAttribute: ") + cudaGetErrorString(e);
@@ -1292,9 +1427,9 @@ cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, cons
                         cudaStream_t s)
 {
     if (w.nh <= 0) return cudaSuccess;
-    k_tc_h<<<(unsigned)w.nh, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.h0,
-                                                          (const uint8_t *)ws + t.img_base,
-                                                          (unsigned long long *)ws, n_split);
+    const int grid = (int)std::min<long long>(w.nh, t.num_sms);
+    k_tc_h<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.h0, (int)w.nh,
+                                                (const uint8_t *)ws + t.img_base, (unsigned long long *)ws, n_split);
     return cudaGetLastError();
 }
 
@@ -1307,19 +1442,31 @@ cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long 
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *d_df,
-                               double offdiag_scale, void *ws, int n_split, cudaStream_t s)
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, double offdiag_scale,
+                               void *ws, int n_split, cudaStream_t s)
 {
     if (w.ng <= 0) return cudaSuccess;
+    const char *base = (const char *)ws;
     k_tc_gather_d<<<(unsigned)w.ng, 256, 0, s>>>(P, t.d_batches, t.d_items + w.g0, (uint8_t *)ws + t.img_base,
-                                                 (const float2 *)d_df, (float)offdiag_scale, n_split);
+                                                 (const float2 *)base, (const unsigned int *)(base + t.bound_off),
+                                                 (const float *)(base + t.bound_off + 4 * t.n_fn),
+                                                 (float)offdiag_scale, n_split);
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_to_df(const double *x, void *out, long long n, cudaStream_t s)
+cudaError_t tc_launch_to_df(const TcPlan &t, const DevPlan &P, const double *x, void *ws, const long long *sys_val0,
+                            const long long *sys_nnz, const int *fn_sys, cudaStream_t s)
 {
-    if (n <= 0) return cudaSuccess;
-    k_to_df<<<1216, 256, 0, s>>>(x, (float2 *)out, n);
+    if (t.nnz <= 0) return cudaSuccess;
+    char *base = (char *)ws;
+    unsigned int *gmax = (unsigned int *)(base + t.bound_off);
+    float *gsum = (float *)(base + t.bound_off + 4 * t.n_fn);
+    cudaError_t e = cudaMemsetAsync(gmax, 0, 8 * (size_t)t.n_fn, s);
+    if (e != cudaSuccess) return e;
+    k_to_df<<<1216, 256, 0, s>>>(x, (float2 *)base, P.rowptr, fn_sys, sys_val0, sys_nnz, t.n_fn, gmax, gsum);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_d_colbounds<<<1216, 256, 0, s>>>((const float2 *)base, P.col_glob, t.nnz, gmax, gsum);
     return cudaGetLastError();
 }
 
@@ -1327,8 +1474,9 @@ cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w
                               int n_split, cudaStream_t s)
 {
     if (w.nd <= 0) return cudaSuccess;
-    k_tc_density<<<(unsigned)w.nd, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.d0,
-                                                                (const uint8_t *)ws + t.img_base, n, n_split);
+    const int grid = (int)std::min<long long>(w.nd, t.num_sms);
+    k_tc_density<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.d0, (int)w.nd,
+                                                      (const uint8_t *)ws + t.img_base, n, n_split);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ struct TcPlanInput {
     const int *atom_nfn = nullptr;
     const char *tune_path = nullptr;
     long long nnz = 0;                   // stored values of H (scratch sizing)
+    long long n_fn = 0;                  // functions (all systems)
     bool host_only = false;              // build host tables only (no device copies)
 };
 
@@ -55,6 +56,9 @@ struct TcPlan {
     size_t ws_bytes = 0;
     size_t wave_cap = 0;
     size_t img_base = 0;                 // workspace offset of the wave images (scratch below)
+    size_t bound_off = 0;                // workspace offset of the per-function bounds of D
+    long long nnz = 0, n_fn = 0;
+    int num_sms = 1;                     // persistent grids: one CTA per SM
     std::vector<TcBatch> batches;
     std::vector<WorkItem> items;
     std::vector<TcWave> waves;
@@ -77,10 +81,12 @@ cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, cons
                         cudaStream_t s);
 cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long long nnz, int accumulate,
                                cudaStream_t s);
-// density: D converted once to double-floats in the scratch, then gathered per batch
-cudaError_t tc_launch_to_df(const double *x, void *out, long long n, cudaStream_t s);
-cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *d_df,
-                               double offdiag_scale, void *ws, int n_split, cudaStream_t s);
+// density: D converted once to double-floats in the scratch (with per-function
+// bounds of |D|), then gathered per batch
+cudaError_t tc_launch_to_df(const TcPlan &t, const DevPlan &P, const double *x, void *ws, const long long *sys_val0,
+                            const long long *sys_nnz, const int *fn_sys, cudaStream_t s);
+cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, double offdiag_scale,
+                               void *ws, int n_split, cudaStream_t s);
 cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
                               double *n, int n_split, cudaStream_t s);
 
