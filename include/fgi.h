@@ -149,6 +149,29 @@ int fgi_workspace_size(fgi_ctx *ctx, size_t *bytes);
 int fgi_integrate_h(fgi_ctx *ctx, const double *v_dev, double *h_dev, int accumulate,
                     void *ws, size_t ws_bytes, void *stream);
 
+/* H integration for callers that cannot allocate device memory (a Fortran
+   SCF driver without a CUDA allocator, a plug-in confined to another
+   framework's memory pool, code that must not allocate inside its loop).
+   The paper has no counterpart: this is a packaging of fgi_integrate_h.
+   Same arguments and results as fgi_integrate_h, but the scratch space is a
+   static device array of FGI_STATIC_SCRATCH_BYTES inside the library, which
+   every GPU that loads the library keeps until the process exits; the call
+   itself allocates nothing (no cudaMalloc, cudaFree or library allocation).
+   - The first call on a device looks up the array's device address (once,
+     with that device current); make that first call before any stream
+     capture.
+   - A plan whose fgi_workspace_size() exceeds FGI_STATIC_SCRATCH_BYTES is
+     rejected with FGI_ERR_WORKSPACE and a message giving both sizes.
+   - All calls on a device share the one array, which keeps the last call's
+     contents (what must start at zero is cleared on the device by each
+     call); calls whose GPU work overlaps (other streams, other host
+     threads, other contexts on the same device) race and must be
+     serialised by the caller.
+   - The launch profile (fgi_profile) does not record this call. */
+#define FGI_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+int fgi_integrate_h_static(fgi_ctx *ctx, const double *v_dev, double *h_dev, int accumulate,
+                           void *stream);
+
 /* Density: n_dev[p] = sum_ij phi_i(r_p) D_ij phi_j(r_p), in the caller's
    point order, D the symmetric matrix whose upper triangle d_dev[nnz]
    (device FP64) stores.  traces_dev (device [n_sys] FP64, may be NULL)

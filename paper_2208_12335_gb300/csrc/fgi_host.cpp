@@ -603,6 +603,74 @@ void wave_work(fgi_ctx *c)
 
 }  // namespace
 
+// ========================================================= internal entry points
+namespace fgi {
+
+int internal_device(const fgi_ctx *c) { return c ? c->device : -1; }
+
+int internal_error(fgi_ctx *c, int code, const char *msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int internal_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void *ws, size_t ws_bytes,
+                         void *stream, bool allow_profile)
+{
+    struct ProfMute {
+        fgi_ctx *c;
+        bool saved;
+        ProfMute(fgi_ctx *c_, bool allow) : c(c_), saved(c_ ? c_->prof_on : false)
+        {
+            if (c && !allow) c->prof_on = false;
+        }
+        ~ProfMute()
+        {
+            if (c) c->prof_on = saved;
+        }
+    } mute(c, allow_profile);
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!v || !h) return set_err(c, FGI_ERR_ARG, "v or h is NULL");
+    if ((rc = check_ws(c, ws, ws_bytes))) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->precision == FGI_FP64) {
+        if (!accumulate) CUDA_TRY(c, cudaMemsetAsync(h, 0, (size_t)c->nnz * sizeof(double), s));
+        DevPlan P = c->dp;
+        P.batches = c->d_batches_f64;
+        for (const Wave &w : c->waves) {
+            {
+                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+                CUDA_TRY(c, launch_phi_f64(P, w.b0, w.nb, (double *)ws, s));
+            }
+            ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
+            CUDA_TRY(c, launch_h_f64(P, c->d_items + w.it0, (int)w.nit, (const double *)ws, v, h, s));
+        }
+        return FGI_OK;
+    }
+    const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+    DevPlan P = c->dp;
+    P.batches = c->d_batches_f64;
+    CUDA_TRY(c, cudaMemsetAsync(ws, 0, (size_t)c->nnz * 8, s));       // fixed-point accumulator
+    for (const TcWave &w : c->tc.waves) {
+        {
+            ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+            CUDA_TRY(c, tc_launch_phi(c->tc, P, w, v, ws, n_split, s));
+        }
+        ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
+        CUDA_TRY(c, tc_launch_h(c->tc, P, w, ws, n_split, s));
+    }
+    {
+        ProfScope ps(c, s, 4, 2.0 * c->nnz, 24.0 * c->nnz);
+        CUDA_TRY(c, tc_launch_fix_to_h(c->tc, ws, h, c->nnz, accumulate, s));
+    }
+    return FGI_OK;
+}
+
+
+}  // namespace fgi
+
 // ================================================================== the ABI
 extern "C" {
 
@@ -843,43 +911,7 @@ int fgi_workspace_size(fgi_ctx *c, size_t *bytes)
 int fgi_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void *ws, size_t ws_bytes,
                     void *stream)
 {
-    int rc = check_compute(c);
-    if (rc) return rc;
-    if (!v || !h) return set_err(c, FGI_ERR_ARG, "v or h is NULL");
-    if ((rc = check_ws(c, ws, ws_bytes))) return rc;
-    DeviceGuard g(c->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (c->precision == FGI_FP64) {
-        if (!accumulate) CUDA_TRY(c, cudaMemsetAsync(h, 0, (size_t)c->nnz * sizeof(double), s));
-        DevPlan P = c->dp;
-        P.batches = c->d_batches_f64;
-        for (const Wave &w : c->waves) {
-            {
-                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
-                CUDA_TRY(c, launch_phi_f64(P, w.b0, w.nb, (double *)ws, s));
-            }
-            ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
-            CUDA_TRY(c, launch_h_f64(P, c->d_items + w.it0, (int)w.nit, (const double *)ws, v, h, s));
-        }
-        return FGI_OK;
-    }
-    const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
-    DevPlan P = c->dp;
-    P.batches = c->d_batches_f64;
-    CUDA_TRY(c, cudaMemsetAsync(ws, 0, (size_t)c->nnz * 8, s));       // fixed-point accumulator
-    for (const TcWave &w : c->tc.waves) {
-        {
-            ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
-            CUDA_TRY(c, tc_launch_phi(c->tc, P, w, v, ws, n_split, s));
-        }
-        ProfScope ps(c, s, 1, w.h_flops, w.h_bytes);
-        CUDA_TRY(c, tc_launch_h(c->tc, P, w, ws, n_split, s));
-    }
-    {
-        ProfScope ps(c, s, 4, 2.0 * c->nnz, 24.0 * c->nnz);
-        CUDA_TRY(c, tc_launch_fix_to_h(c->tc, ws, h, c->nnz, accumulate, s));
-    }
-    return FGI_OK;
+    return fgi::internal_integrate_h(c, v, h, accumulate, ws, ws_bytes, stream, true);
 }
 
 int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws, size_t ws_bytes,

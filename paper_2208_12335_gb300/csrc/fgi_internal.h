@@ -103,3 +103,12 @@ cudaError_t launch_matrix_trace(const DevPlan &P, int n_sys, const long long *sy
 cudaError_t launch_check_finite(const DevPlan &P, const double *x, long long n, cudaStream_t s);
 
 }  // namespace fgi
+
+struct fgi_ctx;
+namespace fgi {
+// host-side helpers shared between the runtime's translation units
+int internal_device(const fgi_ctx *c);
+int internal_error(fgi_ctx *c, int code, const char *msg);
+int internal_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate, void *ws, size_t ws_bytes,
+                         void *stream, bool allow_profile);
+}  // namespace fgi

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfgi.so")
 
 FGI_FP64, FGI_SPLIT_BF16, FGI_BF16 = 0, 1, 2
+FGI_STATIC_SCRATCH_BYTES = 64 << 20          # include/fgi.h
 PRECISIONS = {"fp64": FGI_FP64, "split_bf16": FGI_SPLIT_BF16, "bf16": FGI_BF16}
 ERRORS = {-1: "FGI_ERR_ARG", -2: "FGI_ERR_STATE", -3: "FGI_ERR_CUDA", -4: "FGI_ERR_WORKSPACE",
           -5: "FGI_ERR_TIMEOUT", -6: "FGI_ERR_NONFINITE", -7: "FGI_ERR_UNSUPPORTED",
@@ -26,7 +27,7 @@ SYMBOLS = ["fgi_create", "fgi_destroy", "fgi_last_error", "fgi_add_radial", "fgi
            "fgi_set_systems", "fgi_set_grid", "fgi_plan", "fgi_set_precision", "fgi_get_sizes",
            "fgi_get_system", "fgi_get_pattern", "fgi_workspace_size", "fgi_integrate_h",
            "fgi_density", "fgi_adjoint", "fgi_trace", "fgi_sync", "fgi_profile",
-           "fgi_profile_read"]
+           "fgi_profile_read", "fgi_integrate_h_static"]
 KERNEL_KINDS = {"basis": 0, "h": 1, "density": 2, "adjoint": 3, "other": 4}
 
 
@@ -63,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgi_sync": ([P, P], I),
         "fgi_profile": ([P, I], I),
         "fgi_profile_read": ([P, I, C.POINTER(I64), C.POINTER(D), C.POINTER(D), C.POINTER(D)], I),
+        "fgi_integrate_h_static": ([P, P, P, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
