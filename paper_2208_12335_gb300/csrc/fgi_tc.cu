@@ -717,6 +717,10 @@ constexpr int kWarpProducer = 8, kWarpMma = 9;
 constexpr int kEpiThreads = 256;
 constexpr int kStages = 2;
 constexpr int kStageBytes = 6 * kChunkBytes;     // A and B operands, 3 planes each
+#ifndef FGI_DENSITY_ORDER
+#define FGI_DENSITY_ORDER 2
+#endif
+constexpr int kDensityOrder = FGI_DENSITY_ORDER;  // split products kept in the density (6 of 9)
 
 struct ColRef {                                  // compact column reference for the H scatter
     int gi;                                      // global function
@@ -756,16 +760,17 @@ __device__ __forceinline__ void ring_init(TcRing *S)
     fence_mbar_init();
 }
 
-// issue the split products of one 64-deep chunk (4 k-steps of 16)
+// issue the split products of one 64-deep chunk (4 k-steps of 16): every
+// product of combined order <= max_order except x2*y2; x0*y0 alone in
+// accumulator 0
 __device__ __forceinline__ void mma_chunk(uint32_t acc_base, const uint8_t *a_sm, const uint8_t *b_sm, uint32_t idesc,
-                                         int n_split, bool b_mn, bool *started)
+                                         int n_split, bool b_mn, bool *started, int max_order)
 {
 #pragma unroll
     for (int ks = 0; ks < 4; ks++) {
         for (int pa = 0; pa < n_split; pa++) {
             for (int pb = 0; pb < n_split; pb++) {
-                // split: every product but x2*y2 (x0*y0 alone in accumulator 0)
-                if (pa + pb > 3 || (pa == 2 && pb == 2)) continue;
+                if (pa + pb > max_order || (pa == 2 && pb == 2)) continue;
                 const int acc = (pa + pb == 0) ? 0 : 1;
                 const uint64_t ad = desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
                 const uint64_t bd = b_mn ? desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 2048), 8192, 1024)
@@ -851,7 +856,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     }
                     tc_fence_after();
                     const uint8_t *a_sm = sm + st * kStageBytes;
-                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, false, started);
+                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, false, started, 3);
                     tc_commit(&S->empty[st]);
                 }
                 tc_commit(&S->tfull[buf]);
@@ -1137,7 +1142,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                         }
                         tc_fence_after();
                         const uint8_t *a_sm = sm + st * kStageBytes;
-                        mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started);
+                        mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started,
+                                  kDensityOrder);
                         tc_commit(&S->empty[st]);
                     }
                     tc_commit(&S->tfull[buf]);
@@ -1160,10 +1166,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
             const uint8_t *phi_img = ws + T.img_phi;
             for (int J = 0; J < T.nrb; J++, u++) {
                 const int buf = u & 1, use = u >> 1;
-                ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
-                tc_fence_after();
                 const int r = quad * 32 + lane;
                 const int j = J * 128 + r;
+                // this warp's phi rows for the first of its two column chunks: issued
+                // before the wait so the loads overlap the MMAs
+                uint4 pre[3][4];
+                {
+                    const int cc = 2 * half, c = 2 * m + (cc >> 1);
+#pragma unroll
+                    for (int gg = 0; gg < 4; gg++) {
+                        const long long off = unit_offset(J, T.nc_alloc, c, r, (cc & 1) * 4 + gg);
+#pragma unroll
+                        for (int sp = 0; sp < 3; sp++)
+                            pre[sp][gg] = sp < n_split ? *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi)
+                                                       : make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+                ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
+                tc_fence_after();
                 const uint32_t acc_base = tmem + buf * 256 + lane_base;
                 for (int cq = 0; cq < 2; cq++) {
                     const int cc = 2 * half + cq;
@@ -1188,9 +1208,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     const int g = (cc & 1) * 4 + gg;
                     const long long off = unit_offset(J, T.nc_alloc, c, r, g);
                     uint32_t w[3][4] = {};
-                    for (int sp = 0; sp < n_split; sp++) {
-                        const uint4 u = *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi);
-                        w[sp][0] = u.x; w[sp][1] = u.y; w[sp][2] = u.z; w[sp][3] = u.w;
+#pragma unroll
+                    for (int sp = 0; sp < 3; sp++) {
+                        uint4 uu;
+                        if (cq == 0)
+                            uu = pre[sp][gg];
+                        else
+                            uu = sp < n_split ? *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi)
+                                              : make_uint4(0u, 0u, 0u, 0u);
+                        w[sp][0] = uu.x; w[sp][1] = uu.y; w[sp][2] = uu.z; w[sp][3] = uu.w;
                     }
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
