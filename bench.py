@@ -36,16 +36,24 @@ METRIC = "grid pts/s and TFLOP/s for H-integ+density on 1 GB300, split-BF16 vs F
 UNIT = "grid_pts/s"
 
 
-def make_workload(name):
+def make_workload(name, accel=None):
+    """The synthetic workloads; accel='cuda' builds partition weights and
+    potentials with torch on the GPU (same definitions, faster)."""
     if name == "tiny":
         return W.tiny_water(), "tiny water: 3 atoms, 7 fns, 40x110 pts/atom"
     if name == "si64":
-        return W.si64(), "Si64 cluster: 64 atoms, 1600 fns (6s3p2d), 60x302 pts/atom, batches <=300 pts"
+        return (W.si64(accel=accel),
+                "Si64 cluster: 64 atoms, 1600 fns (6s3p2d), 60x302 pts/atom, batches <=300 pts")
     if name == "chno1000":
-        return W.chno_cluster(), "1000-atom CHNO cluster, 70x590 pts/atom, uneven batches 50-400 pts"
+        return (W.chno_cluster(accel=accel),
+                "1000-atom CHNO cluster, 19 fns/heavy atom, 5/H, 70x590 pts/atom, uneven batches 50-400 pts")
     if name.startswith("chno"):
         n = int(name[4:])
-        return W.chno_cluster(n_atoms=n), "%d-atom CHNO cluster" % n
+        return W.chno_cluster(n_atoms=n, accel=accel), "%d-atom CHNO cluster, 70x590 pts/atom" % n
+    if name.startswith("many"):
+        n = int(name[4:] or 512)
+        return (W.many_molecules(n_mol=n, accel=accel),
+                "%d independent CHNO molecules of 5-40 atoms, 30-60 x 110-302 pts/atom" % n)
     raise SystemExit("unknown workload " + name)
 
 
@@ -247,7 +255,7 @@ def main():
     dev = torch.device("cuda:%d" % local)
     from paper_2208_12335_gb300 import Context
 
-    prob, desc = make_workload(args.workload)
+    prob, desc = make_workload(args.workload, accel="cuda")
     if args.batches:
         ids = np.sort(np.random.default_rng(99).choice(prob.n_batch, size=min(args.batches, prob.n_batch),
                                                         replace=False))

@@ -184,7 +184,10 @@ int fgi_density(fgi_ctx *ctx, const double *d_dev, double *n_dev, double *traces
    G_ii = g_ii, G_ij = G_ji = g_ij/2, and the grid held fixed while atoms move,
      dv_dev[p]   = w_p sum_ij G_ij phi_i phi_j                      [n_pts]
      dR_dev[a,:] = -2 sum_p w_p v_p sum_{i on a} grad phi_i . (G phi)_i  [n_atoms][3]
-   v_dev is the potential of the forward call.  All device FP64. */
+   v_dev is the potential of the forward call.  All device FP64.  The
+   adjoint is computed on the FP64 path whatever the context's precision;
+   the basis and its gradient are recomputed per batch (nothing is kept from
+   the forward call). */
 int fgi_adjoint(fgi_ctx *ctx, const double *g_dev, const double *v_dev, double *dv_dev,
                 double *dR_dev, void *ws, size_t ws_bytes, void *stream);
 

@@ -303,6 +303,68 @@ def becke_partition(pts, owner, atom_xyz, k_near=12, chunk=40000):
     return out
 
 
+def _torch_device(accel):
+    """torch device for the accelerated generator paths (None: numpy)."""
+    if not accel:
+        return None
+    import torch
+    if accel == "cuda" and not torch.cuda.is_available():
+        return torch.device("cpu")
+    return torch.device(accel)
+
+
+def becke_partition_torch(pts, owner, atom_xyz, dev, k_near=12, chunk=200000):
+    """Becke cell weight P_owner / sum_C P_C (same definition as becke_partition)
+    with torch in float64 on `dev`: the owning atom plus its k nearest atoms."""
+    import torch
+    A = torch.as_tensor(atom_xyz, dtype=torch.float64, device=dev)
+    n_at = A.shape[0]
+    k = min(k_near, n_at)
+    rab = torch.cdist(A, A)
+    out = np.empty(len(pts))
+    if n_at == 1:
+        out[:] = 1.0
+        return out
+    for c0 in range(0, len(pts), chunk):
+        p = torch.as_tensor(pts[c0:c0 + chunk], dtype=torch.float64, device=dev)
+        own = torch.as_tensor(owner[c0:c0 + chunk], dtype=torch.int64, device=dev)
+        dall = torch.cdist(p, A)                                             # (n, n_at)
+        idx = torch.topk(dall, k, dim=1, largest=False).indices              # nearest k
+        has = (idx == own[:, None]).any(dim=1)
+        idx[~has, -1] = own[~has]
+        d = torch.gather(dall, 1, idx)
+        R = rab[idx[:, :, None], idx[:, None, :]]
+        mu = torch.where(R > 0, (d[:, :, None] - d[:, None, :]) / torch.where(R > 0, R, 1.0), 0.0)
+        f = mu
+        for _ in range(3):
+            f = 1.5 * f - 0.5 * f * f * f
+        s = 0.5 * (1.0 - f)
+        eye = torch.eye(k, dtype=torch.bool, device=dev)
+        s = torch.where(eye[None], 1.0, s)
+        P = torch.prod(s, dim=2)
+        pown = (P * (idx == own[:, None])).sum(dim=1)
+        out[c0:c0 + chunk] = (pown / P.sum(dim=1)).cpu().numpy()
+    return out
+
+
+def coulomb_potential_torch(pts, atom_xyz, Z, dev, v_cut, screened, chunk=20000):
+    """Same function as coulomb_erf_potential, with torch in float64 on `dev`."""
+    import torch
+    A = torch.as_tensor(atom_xyz, dtype=torch.float64, device=dev)
+    Zt = torch.as_tensor(Z, dtype=torch.float64, device=dev)
+    c = 2.0 / math.sqrt(math.pi) * (0.5 if screened else 1.0)
+    v = np.empty(len(pts))
+    for c0 in range(0, len(pts), chunk):
+        p = torch.as_tensor(pts[c0:c0 + chunk], dtype=torch.float64, device=dev)
+        d = torch.cdist(p, A)
+        num = torch.erf(d) - torch.erf(0.5 * d) if screened else torch.erf(d)
+        f = torch.where(d > 1e-12, num / torch.where(d > 1e-12, d, 1.0), c)
+        if v_cut is not None:
+            f = torch.where(d < v_cut, f, 0.0)
+        v[c0:c0 + chunk] = -(f * Zt[None, :]).sum(dim=1).cpu().numpy()
+    return v
+
+
 def bisect_batches(xyz, p_max, p_min, rng=None, q_range=(0.5, 0.5)):
     """Recursive bisection; returns a list of index arrays (depth-first)."""
     leaves = []
@@ -359,7 +421,7 @@ def coulomb_erf_potential(pts, atom_xyz, Z, v_cut=None, chunk=200000, screened=F
 
 
 def build_problem(name, radials, species, systems, grid_spec, workload_index,
-                  batch_spec, v_full_atoms=200, v_cut=15.0, becke_k=12, screened=True):
+                  batch_spec, v_full_atoms=200, v_cut=15.0, becke_k=12, screened=True, accel=None):
     """Assemble a Problem from per-system geometries.
 
     systems: list of (species_index_array, xyz_bohr_array)
@@ -385,12 +447,19 @@ def build_problem(name, radials, species, systems, grid_spec, workload_index,
         pts = np.concatenate(pts_l)
         w = np.concatenate(w_l)
         own = np.concatenate(own_l)
-        w = w * becke_partition(pts, own, xyz, k_near=becke_k)
+        dev = _torch_device(accel)
+        if dev is None:
+            w = w * becke_partition(pts, own, xyz, k_near=becke_k)
+        else:
+            w = w * becke_partition_torch(pts, own, xyz, dev, k_near=becke_k)
         keep = w >= 1e-18
         pts, w = pts[keep], w[keep]
         Zs = np.array([species[k].Z for k in sp_idx])
-        v = coulomb_erf_potential(pts, xyz, Zs, None if len(xyz) <= v_full_atoms else v_cut,
-                                  screened=screened)
+        vc = None if len(xyz) <= v_full_atoms else v_cut
+        if dev is None:
+            v = coulomb_erf_potential(pts, xyz, Zs, vc, screened=screened)
+        else:
+            v = coulomb_potential_torch(pts, xyz, Zs, dev, vc, screened)
         leaves = bisect_batches(pts, p_max, p_min, rng_bat if q_range else None,
                                 q_range if q_range else (0.5, 0.5))
         order = np.concatenate(leaves)
@@ -464,7 +533,8 @@ SI_ALPHA = {0: [(4.0, 8.0), (1.5, 3.0), (0.6, 1.2), (0.3, 0.6), (0.15, 0.3), (0.
             2: [(0.5, 1.2), (0.15, 0.4)]}
 
 
-def si64(n_rad=60, n_ang=302, p_max=300, p_min=100, workload_index=1, cells=2, jitter_ang=0.05):
+def si64(n_rad=60, n_ang=302, p_max=300, p_min=100, workload_index=1, cells=2, jitter_ang=0.05,
+         accel=None):
     """Si diamond cluster (2x2x2 conventional cells, 64 atoms), 25 fns/atom.
 
     The workload names 4s,3p,2d shells and 25 fns/atom; with real spherical
@@ -491,7 +561,7 @@ def si64(n_rad=60, n_ang=302, p_max=300, p_min=100, workload_index=1, cells=2, j
     species = [Species("Si", 14.0, list(range(len(radials))))]
     systems = [(np.zeros(len(xyz), dtype=np.int32), xyz)]
     return build_problem("si64", radials, species, systems, lambda sp: (n_rad, n_ang),
-                         workload_index, (p_max, p_min, None))
+                         workload_index, (p_max, p_min, None), accel=accel)
 
 
 HEAVY_ALPHA = {0: [(4.0, 8.0), (1.5, 3.0), (0.6, 1.2), (0.25, 0.5), (0.1, 0.2)],
@@ -545,7 +615,7 @@ def chno_species(rng, r_cut_ang=5.0):
 
 
 def chno_cluster(n_atoms=1000, n_rad=70, n_ang=590, p_max=400, p_min=50, workload_index=2,
-                 atoms_with_grid=None):
+                 atoms_with_grid=None, accel=None):
     """Random organic-like C/H/N/O cluster; uneven batches.
 
     atoms_with_grid: optional list of atom indices whose atom-centred grids
@@ -561,14 +631,14 @@ def chno_cluster(n_atoms=1000, n_rad=70, n_ang=590, p_max=400, p_min=50, workloa
     xyz = pos * BOHR_PER_ANG
     return build_problem_grid_subset("chno%d" % n_atoms, radials, species, sp_idx, xyz,
                                      (n_rad, n_ang), workload_index, (p_max, p_min, (0.2, 0.8)),
-                                     atoms_with_grid)
+                                     atoms_with_grid, accel)
 
 
 def build_problem_grid_subset(name, radials, species, sp_idx, xyz, nrad_nang, workload_index,
-                              batch_spec, atoms_with_grid):
+                              batch_spec, atoms_with_grid, accel=None):
     if atoms_with_grid is None:
         return build_problem(name, radials, species, [(sp_idx, xyz)], lambda sp: nrad_nang,
-                             workload_index, batch_spec)
+                             workload_index, batch_spec, accel=accel)
     # generate only the listed atoms' grids (same rotations as the full build
     # would give those atoms only if every atom is listed; this is a separate,
     # smaller workload over the same geometry)
@@ -599,7 +669,7 @@ def build_problem_grid_subset(name, radials, species, sp_idx, xyz, nrad_nang, wo
 
 
 def many_molecules(n_mol=512, workload_index=4, n_at_range=(5, 40), nrad_range=(30, 60),
-                   nang_choices=(110, 146, 194, 230, 266, 302), p_max=300, p_min=50):
+                   nang_choices=(110, 146, 194, 230, 266, 302), p_max=300, p_min=50, accel=None):
     """Many independent small H/C/N/O molecules integrated together."""
     rng_g = rng_for(workload_index, PURPOSE_GEOMETRY)
     rng_b = rng_for(workload_index, PURPOSE_BASIS)
@@ -615,7 +685,7 @@ def many_molecules(n_mol=512, workload_index=4, n_at_range=(5, 40), nrad_range=(
                       int(nang_choices[int(rng_g.integers(0, len(nang_choices)))])))
     # per-molecule grid sizes: build each system separately then merge
     parts = [build_problem("mol", radials, species, [systems[m]], (lambda sp, g=grids[m]: g),
-                           workload_index * 1000 + m, (p_max, p_min, None))
+                           workload_index * 1000 + m, (p_max, p_min, None), accel=accel)
              for m in range(n_mol)]
     return merge_problems("many%d" % n_mol, parts, workload_index)
 
