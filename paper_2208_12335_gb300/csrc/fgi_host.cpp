@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -100,7 +101,8 @@ struct fgi_ctx {
     long long *d_sys_val0 = nullptr, *d_sys_fn0 = nullptr, *d_sys_nnz = nullptr;
     int *d_fn_sys = nullptr;
     int *d_status = nullptr;
-    TcPlan tc;                                // tensor-core path plan
+    TcPlan tc;                                // tensor-core plan of the H integration (the batches as given)
+    TcPlan tcd;                               // tensor-core plan of the density (super-batches)
     // per-kernel CUDA-event profile
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -149,6 +151,7 @@ void free_device(fgi_ctx *c)
     c->d_arena = nullptr;
     c->arena_bytes = 0;
     tc_free(c->tc);
+    tc_free(c->tcd);
     c->planned = false;
 }
 
@@ -163,6 +166,22 @@ void invalidate(fgi_ctx *c)
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void wave_work(fgi_ctx *c);
+
+// Two tensor-core plans: H keeps the batches as given (its split accuracy
+// depends on the points per contraction), the density merges neighbouring
+// batches into super-batches of up to 1024 points (its accuracy does not).
+int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
+{
+    tin.sb_points = 0;
+    tin.sb_growth = 1.0;
+    int rc = tc_build(c->tc, tin, err);
+    if (rc != FGI_OK) return rc;
+    tin.sb_points = 1024;
+    tin.sb_growth = 1.35;
+    if (const char *e = getenv("FGI_SB_POINTS")) tin.sb_points = atoi(e);
+    if (const char *e = getenv("FGI_SB_GROWTH")) tin.sb_growth = atof(e);
+    return tc_build(c->tcd, tin, err);
+}
 
 // ------------------------------------------------------------ plan building
 int build_plan(fgi_ctx *c, const char *tune_path)
@@ -358,7 +377,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         tin.n_fn = c->n_fn;
         tin.host_only = true;
         std::string terr;
-        int rc = tc_build(c->tc, tin, &terr);
+        int rc = build_tc_plans(c, tin, &terr);
         if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
         c->planned = true;
         return FGI_OK;
@@ -523,7 +542,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     tin.nnz = c->nnz;
     tin.n_fn = c->n_fn;
     std::string terr;
-    int rc = tc_build(c->tc, tin, &terr);
+    int rc = build_tc_plans(c, tin, &terr);
     if (rc != FGI_OK) return set_err(c, rc, "%s", terr.c_str());
     c->planned = true;
     return FGI_OK;
@@ -544,7 +563,10 @@ int check_compute(fgi_ctx *c)
     return FGI_OK;
 }
 
-size_t workspace_need(fgi_ctx *c) { return std::max(c->ws_f64_bytes, tc_workspace_bytes(c->tc)); }
+size_t workspace_need(fgi_ctx *c)
+{
+    return std::max(c->ws_f64_bytes, std::max(tc_workspace_bytes(c->tc), tc_workspace_bytes(c->tcd)));
+}
 
 int check_ws(fgi_ctx *c, void *ws, size_t bytes)
 {
@@ -651,7 +673,8 @@ int internal_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate,
     }
     const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
     DevPlan P = c->dp;
-    P.batches = c->d_batches_f64;
+    P.batches = c->tc.d_sb;
+    P.act = c->tc.d_sact;
     CUDA_TRY(c, cudaMemsetAsync(ws, 0, (size_t)c->nnz * 8, s));       // fixed-point accumulator
     for (const TcWave &w : c->tc.waves) {
         {
@@ -938,21 +961,24 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
         }
     } else {
         const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+        DevPlan Q = c->dp;
+        Q.batches = c->tcd.d_sb;
+        Q.act = c->tcd.d_sact;
         {
             ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz);
-            CUDA_TRY(c, tc_launch_to_df(c->tc, P, d, ws, c->d_sys_val0, c->d_sys_nnz, c->d_fn_sys, s));
+            CUDA_TRY(c, tc_launch_to_df(c->tcd, Q, d, ws, c->d_sys_val0, c->d_sys_nnz, c->d_fn_sys, s));
         }
-        for (const TcWave &w : c->tc.waves) {
+        for (const TcWave &w : c->tcd.waves) {
             {
                 ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
-                CUDA_TRY(c, tc_launch_phi_cols(c->tc, P, w, ws, n_split, s));
+                CUDA_TRY(c, tc_launch_phi_cols(c->tcd, Q, w, ws, n_split, s));
             }
             {
                 ProfScope ps(c, s, 4, 0.0, w.g_bytes);
-                CUDA_TRY(c, tc_launch_gather_d(c->tc, P, w, 1.0, ws, n_split, s));
+                CUDA_TRY(c, tc_launch_gather_d(c->tcd, Q, w, 1.0, ws, n_split, s));
             }
             ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
-            CUDA_TRY(c, tc_launch_density(c->tc, P, w, ws, n, n_split, s));
+            CUDA_TRY(c, tc_launch_density(c->tcd, Q, w, ws, n, n_split, s));
         }
     }
     if (traces) {

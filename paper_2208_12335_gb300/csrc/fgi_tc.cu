@@ -390,6 +390,9 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
         ipow[2] = df_mul(ipow[1], ipow[0]);
         ipow[3] = df_mul(ipow[2], ipow[0]);
         int f = 0;
+        // knot interval and offset, shared by consecutive shells on the same knot grid
+        float grid_hi = -1.f, grid_lo = 0.f, t = 0.f;
+        int grid_nk = -1, kk = 0;
         for (int sh = 0; sh < S.n_shell; sh++) {
             const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
             const int nm = 2 * R.l + 1;
@@ -407,10 +410,15 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                 } else {
                     // t = frac(d/h) from the double-float d; u = c0 + t (c1 + t (c2 + t c3))
                     // with c0 in double-float and the (smaller) polynomial tail in FP32
-                    const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
-                    int kk = (int)floorf(s.hi);
-                    kk = max(0, min(kk, R.nk - 2));
-                    const float t = (s.hi - (float)kk) + s.lo;
+                    if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
+                        grid_hi = R.inv_h_hi;
+                        grid_lo = R.inv_h_lo;
+                        grid_nk = R.nk;
+                        const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
+                        kk = (int)floorf(s.hi);
+                        kk = max(0, min(kk, R.nk - 2));
+                        t = (s.hi - (float)kk) + s.lo;
+                    }
                     const float4 ch = __ldg(P.coef_dd + 2 * (R.coef_off + kk));
                     const float c0lo = __ldg(reinterpret_cast<const float *>(P.coef_dd + 2 * (R.coef_off + kk) + 1));
                     const float tail = t * (ch.y + t * (ch.z + t * ch.w));
@@ -451,7 +459,9 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 // coordinates; only the angular polynomial Q_lm(x, y, z) is FP32 (its
 // rounding varies from point to point).
 
-__global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+constexpr int kPhiThreads = 256;
+
+__global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed)
 {
     extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
@@ -534,8 +544,8 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
             }
         }
         __syncthreads();
-        if (threadIdx.x < 256) {
-            const int which = threadIdx.x >> 7, r = threadIdx.x & 127;
+        for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+            const int which = q >> 7, r = q & 127;
             float sc, un;
             fixed_scale_adaptive(__uint_as_float(rowmax[which][r]), rowsum[which][r], T.nc * 64, sc, un);
             fsc[which][r][0] = sc;
@@ -592,7 +602,7 @@ __global__ void __launch_bounds__(256) k_tc_phi(DevPlan P, const TcBatch *tb, co
 // density contracts over functions, so the fixed-point grid of the leading
 // term is per point (column): first the largest |phi_i(p)| over all of the
 // batch's functions (FP32), then every 128-row block in double-float.
-__global__ void __launch_bounds__(256) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                      uint8_t *ws, int n_split)
 {
     extern __shared__ float2 phi_smem[];
@@ -942,19 +952,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
 // K-major swizzled image.  In the split mode the leading term is fixed-point
 // on a per-row grid (the density contracts over i), found by a first pass
 // over the row block.
-__device__ __forceinline__ df gather_d_value(const int *pp_sys, int nat, int nfn, const FnRef &rj, const FnRef &ci,
-                                             int j, int i, const float2 *ddv, float offdiag_scale)
-{
-    if (j >= nfn || i >= nfn) return df{0.f, 0.f};
-    const FnRef &a = (i <= j) ? ci : rj;
-    const FnRef &b = (i <= j) ? rj : ci;
-    const long long k = value_index_pp(pp_sys, nat, a, b);
-    if (k < 0) return df{0.f, 0.f};
-    const float2 v = __ldg(ddv + k);
-    const float sc = i == j ? 1.f : offdiag_scale;     // 1 or 1/2: exact
-    return df{v.x * sc, v.y * sc};
-}
-
 // D values as double-floats (once per density call; nnz elements), and for
 // every function g the largest |D_gi| and the sum of |D_gi| over its full
 // symmetric row: bounds (valid for every batch) for the fixed-point grid of
@@ -1038,11 +1035,44 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
         for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
             const int r = u >> 3, g = u & 7;
             const int j = J * 128 + r;
+            const FnRef rj = rref[r];
+            // stored value of (j, i): for i >= j, base + gi (row j's run of atom(i));
+            // for i < j, rp_i - li + off (row i's run of atom(j)); cached per column atom
+            int cur_atom = -1;
+            long long off = 0;
+            bool stored = false;
             df x[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const int il = g * 8 + q;
-                x[q] = gather_d_value(pp_sys, nat, B.nfn, rref[r], cref[il], j, kc * 64 + il, ddv, offdiag_scale);
+                const int i = kc * 64 + il;
+                x[q] = df{0.f, 0.f};
+                if (j >= B.nfn || i >= B.nfn) continue;
+                const FnRef &ci = cref[il];
+                if (ci.atom != cur_atom) {
+                    cur_atom = ci.atom;
+                    if (ci.atom == rj.atom) {
+                        stored = true;
+                        off = 0;
+                    } else if (ci.atom > rj.atom) {
+                        const int pp = __ldg(pp_sys + (long long)rj.loc * nat + ci.loc);
+                        stored = pp >= 0;
+                        off = rj.rp + pp - rj.li - (ci.gi - ci.li);       // + gi
+                    } else {
+                        const int pp = __ldg(pp_sys + (long long)ci.loc * nat + rj.loc);
+                        stored = pp >= 0;
+                        off = pp + rj.li;                                   // + rp_i - li
+                    }
+                }
+                if (!stored) continue;
+                long long k;
+                if (ci.atom == rj.atom)
+                    k = i >= j ? rj.rp + (ci.gi - rj.gi) : ci.rp + (rj.gi - ci.gi);
+                else
+                    k = ci.atom > rj.atom ? off + ci.gi : ci.rp - ci.li + off;
+                const float2 v = __ldg(ddv + k);
+                const float sc = i == j ? 1.f : offdiag_scale;
+                x[q] = df{v.x * sc, v.y * sc};
             }
             uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
             if (fixed)
@@ -1296,19 +1326,77 @@ cudaError_t set_attrs()
 }  // namespace
 
 // ==================================================================== host
+// Super-batches: runs of consecutive batches of one system (the batcher
+// emits spatial neighbours consecutively), merged while the points stay
+// within sb_points and the union of active atoms carries at most
+// sb_growth times the functions of the largest member.  Every sum of the
+// method is over points, so any grouping of points gives the same H and n;
+// merging cuts the per-batch scatter, D gather and tile overheads.
+static void build_super_batches(TcPlan &t, const TcPlanInput &in, int sb_points, double sb_growth)
+{
+    t.sb.clear();
+    t.sact.clear();
+    std::vector<int> uni, tmp;
+    int b = 0;
+    while (b < in.n_batch) {
+        const DevBatch &B0 = in.batches[b];
+        uni.clear();
+        for (int e = 0; e < B0.n_act; e++) uni.push_back(in.act[B0.act0 + e].atom);
+        int np = B0.np, maxfn = B0.nfn, b2 = b + 1;
+        while (sb_points > 0 && b2 < in.n_batch && in.batches[b2].sys == B0.sys &&
+               np + in.batches[b2].np <= sb_points) {
+            const DevBatch &Bn = in.batches[b2];
+            tmp.clear();
+            size_t i = 0;
+            int e = 0;
+            while (i < uni.size() || e < Bn.n_act) {
+                const int a = e < Bn.n_act ? in.act[Bn.act0 + e].atom : 1 << 30;
+                const int u = i < uni.size() ? uni[i] : 1 << 30;
+                if (u == a) { tmp.push_back(u); i++; e++; }
+                else if (u < a) { tmp.push_back(u); i++; }
+                else { tmp.push_back(a); e++; }
+            }
+            long long nfn = 0;
+            for (int a : tmp) nfn += in.atom_nfn[a];
+            const int mx = std::max(maxfn, Bn.nfn);
+            if (nfn > sb_growth * mx || nfn > kMaxBatchFns) break;
+            uni.swap(tmp);
+            np += Bn.np;
+            maxfn = mx;
+            b2++;
+        }
+        DevBatch S{};
+        S.pt0 = B0.pt0;
+        S.np = np;
+        S.sys = B0.sys;
+        S.act0 = (int)t.sact.size();
+        S.n_act = (int)uni.size();
+        int fl = 0;
+        for (int a : uni) {
+            t.sact.push_back(DevAct{a, fl});
+            fl += in.atom_nfn[a];
+        }
+        S.nfn = fl;
+        t.sb.push_back(S);
+        b = b2;
+    }
+}
+
 int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
 {
     tc_free(t);
-    t.batches.assign(in.n_batch, TcBatch{});
+    build_super_batches(t, in, std::min(in.sb_points, kMaxBatchPoints), std::max(1.0, in.sb_growth));
+    const int n_sb = (int)t.sb.size();
+    t.batches.assign(n_sb, TcBatch{});
     t.items.clear();
     t.waves.clear();
     size_t cap = (size_t)24 << 30;   // workloads up to ~24 GB of operand images run as one wave
     if (const char *e = getenv("FGI_TC_WAVE_MB")) cap = (size_t)std::max(1L, atol(e)) << 20;
     t.wave_cap = cap;
     // per-batch image geometry and footprint (3 planes always reserved)
-    std::vector<size_t> foot(in.n_batch, 0);
-    for (int b = 0; b < in.n_batch; b++) {
-        const DevBatch &B = in.batches[b];
+    std::vector<size_t> foot(n_sb, 0);
+    for (int b = 0; b < n_sb; b++) {
+        const DevBatch &B = t.sb[b];
         TcBatch &T = t.batches[b];
         T.nrb = (B.nfn + 127) / 128;
         T.nc = (B.np + 63) / 64;
@@ -1327,7 +1415,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         max_ws = std::max(max_ws, off);
         t.waves.push_back(w);
     };
-    for (int b = 0; b < in.n_batch; b++) {
+    for (int b = 0; b < n_sb; b++) {
         if (b > w.b0 && off + foot[b] > cap) {
             close_wave(b);
             w = TcWave{};
@@ -1339,9 +1427,9 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         T.img_aux = (long long)(off + 3 * (size_t)T.plane_phi);
         off += foot[b];
     }
-    close_wave(in.n_batch);
+    close_wave(n_sb);
     for (TcWave &wv : t.waves) {
-        auto live = [&](int b) { return in.batches[b].np > 0 && in.batches[b].nfn > 0; };
+        auto live = [&](int b) { return t.sb[b].np > 0 && t.sb[b].nfn > 0; };
         wv.phi0 = (long long)t.items.size();
         for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
             if (live(b))
@@ -1370,7 +1458,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         }
         wv.nd = (long long)t.items.size() - wv.d0;
         for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
-            const double P = in.batches[b].np, n = in.batches[b].nfn;
+            const double P = t.sb[b].np, n = t.sb[b].nfn;
             wv.phi_flops += 30.0 * P * n;
             wv.phi_bytes += 32.0 * P + 12.0 * P * n;
             wv.h_flops += P * n * (n + 1.0);
@@ -1391,7 +1479,10 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
     if (!in.host_only) {
         const size_t nb_bytes = t.batches.size() * sizeof(TcBatch);
         const size_t ni_bytes = t.items.size() * sizeof(WorkItem);
-        const size_t tot = ((nb_bytes + 255) / 256) * 256 + ni_bytes + 256;
+        const size_t sb_bytes = t.sb.size() * sizeof(DevBatch);
+        const size_t sa_bytes = t.sact.size() * sizeof(DevAct);
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        const size_t tot = al(nb_bytes) + al(ni_bytes) + al(sb_bytes) + al(sa_bytes) + 256;
         cudaError_t e = cudaMalloc(&t.d_mem, tot);
         if (e != cudaSuccess) {
             t.d_mem = nullptr;
@@ -1404,6 +1495,11 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         if (ni_bytes) cudaMemcpy(base + ioff, t.items.data(), ni_bytes, cudaMemcpyHostToDevice);
         t.d_batches = (const TcBatch *)base;
         t.d_items = (const WorkItem *)(base + ioff);
+        const size_t soff = ioff + al(ni_bytes), aoff = soff + al(sb_bytes);
+        if (sb_bytes) cudaMemcpy(base + soff, t.sb.data(), sb_bytes, cudaMemcpyHostToDevice);
+        if (sa_bytes) cudaMemcpy(base + aoff, t.sact.data(), sa_bytes, cudaMemcpyHostToDevice);
+        t.d_sb = (const DevBatch *)(base + soff);
+        t.d_sact = (const DevAct *)(base + aoff);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1435,7 +1531,7 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     if (w.nphi <= 0) return cudaSuccess;
     // the H images (v given) of the split mode use the fixed-point leading term
     const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
-    k_tc_phi<<<(unsigned)w.nphi, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
+    k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
                                                        (uint8_t *)ws + t.img_base, v, n_split, fixed);
     return cudaGetLastError();
 }
@@ -1444,7 +1540,7 @@ cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &
                                cudaStream_t s)
 {
     if (w.npc <= 0) return cudaSuccess;
-    k_tc_phi_cols<<<(unsigned)w.npc, 256, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0,
+    k_tc_phi_cols<<<(unsigned)w.npc, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0,
                                                            (uint8_t *)ws + t.img_base, n_split);
     return cudaGetLastError();
 }

@@ -47,6 +47,8 @@ struct TcPlanInput {
     const int *atom_nfn = nullptr;
     const char *tune_path = nullptr;
     long long nnz = 0;                   // stored values of H (scratch sizing)
+    int sb_points = 0;                   // super-batch point limit (0: keep the batches)
+    double sb_growth = 1.0;              // limit on the union's functions / largest member's
     long long n_fn = 0;                  // functions (all systems)
     bool host_only = false;              // build host tables only (no device copies)
 };
@@ -59,7 +61,11 @@ struct TcPlan {
     size_t bound_off = 0;                // workspace offset of the per-function bounds of D
     long long nnz = 0, n_fn = 0;
     int num_sms = 1;                     // persistent grids: one CTA per SM
-    std::vector<TcBatch> batches;
+    std::vector<DevBatch> sb;            // super-batches (points, union of active atoms)
+    std::vector<DevAct> sact;            // their active-atom entries
+    const DevBatch *d_sb = nullptr;
+    const DevAct *d_sact = nullptr;
+    std::vector<TcBatch> batches;        // per super-batch image geometry
     std::vector<WorkItem> items;
     std::vector<TcWave> waves;
     void *d_mem = nullptr;               // device copies of batches + items
