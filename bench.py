@@ -153,6 +153,12 @@ def fp64_gemm_peak(torch):
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
+def fp32_alu_peak(torch, mhz):
+    """FP32 FMA issue rate of the device: SMs x 128 lanes x 2 FLOP per clock."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def traffic_for(kind):
     """dram bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
@@ -385,16 +391,22 @@ def main():
             per_launch_flops = pk["flops"] / max(1, pk["launches"])
             per_launch_bytes = pk["bytes"] / max(1, pk["launches"])
             if dom == "basis":
-                ach = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-                peak = peaks["hbm_gbs"]
-                roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s"}
+                # FP32 pipe: 152 SMs x 128 lanes x 2 FLOP (FMA) per clock at the
+                # sampled maximum SM clock; the algorithmic count is ~30 FLOP
+                # per (point, function)
+                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
+                mhz = clk.summary().get("sm_max_mhz") or 2070.0
+                peak = fp32_alu_peak(torch, mhz)
+                roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "peak_note": "FP32 FMA issue rate: SMs x 128 lanes x 2 FLOP x %.0f MHz" % mhz}
             elif args.precision == "fp64":
                 ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
                 peak = fp64_gemm_peak(torch)
                 roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                         "peak_note": "measured FP64 GEMM (cuBLAS) on this GPU"}
             else:
-                products = 8 if args.precision == "split_bf16" else 1
+                # BF16 products per algorithmic FLOP: split H 8, split density 6
+                products = ({"h": 8, "density": 6}[dom] if args.precision == "split_bf16" else 1)
                 ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
                 peak = peaks["bf16_tflops_sustained"] / products
                 roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",

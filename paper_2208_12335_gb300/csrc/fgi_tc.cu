@@ -360,6 +360,32 @@ __device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const flo
 
 constexpr int kPhiValStride = 33;   // float2 per row of phi_smem (32 points + padding)
 
+// The 2l+1 values N_lm u(d)/d^(l+1) Q_lm(x, y, z) of one shell (functions
+// f0 .. f0+2l of the atom; only those in [f_lo, f_hi) are written): the
+// radial factor times each distinct constant in double-float, times the
+// FP32 polynomial.  Unrolled per l so that everything stays in registers.
+template <int L>
+__device__ __forceinline__ void emit_shell(df rad, float x, float y, float z, float2 *out, int f0, int f_lo,
+                                           int f_hi)
+{
+    constexpr int NM = 2 * L + 1;
+    float Q[7];
+    int ci[7];
+    ylm_poly_f32(L, x, y, z, Q, ci);
+    constexpr int NC = L < 2 ? 1 : (L == 2 ? 3 : 5);
+    constexpr int C0 = L == 0 ? 0 : (L == 1 ? 1 : (L == 2 ? 2 : 5));
+    df rc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) rc[c] = df_mul(rad, df{kYlmC[C0 + c].x, kYlmC[C0 + c].y});
+#pragma unroll
+    for (int m = 0; m < NM; m++) {
+        const int fm = f0 + m;
+        if (fm < f_lo || fm >= f_hi) continue;
+        const df val = df_mul_f(rc[ci[m] - C0], Q[m]);
+        out[fm * kPhiValStride] = make_float2(val.hi, val.lo);
+    }
+}
+
 // Double-float phi for rows [r0, r0+128) (atoms e0..e0+ne-1 of the batch)
 // at the 32 points p0..p0+31, into phi_smem[row - r0][point - p0] (zero for
 // points beyond the batch).
@@ -424,26 +450,17 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                     const float tail = t * (ch.y + t * (ch.z + t * ch.w));
                     df uu = df_two_sum(ch.x, tail);
                     uu = df_fast_two_sum(uu.hi, uu.lo + c0lo);
-                    rad = df_mul(uu, ipow[R.l]);
+                    const df ip = R.l == 0 ? ipow[0] : (R.l == 1 ? ipow[1] : (R.l == 2 ? ipow[2] : ipow[3]));
+                    rad = df_mul(uu, ip);
                 }
             }
-            float Q[7];
-            int ci[7];
-            ylm_poly_f32(R.l, x.hi, y.hi, z.hi, Q, ci);
-            // radial factor times each distinct normalisation constant of the shell
-            df rc[5];
-            const int cbase = ci[0];
-            const int ncst = R.l < 2 ? 1 : (R.l == 2 ? 3 : 5);
-            for (int q = 0; q < ncst; q++) {
-                const float2 cc = kYlmC[R.l == 2 ? 2 + q : (R.l == 3 ? 5 + q : cbase)];
-                rc[q] = df_mul(rad, df{cc.x, cc.y});
+            switch (R.l) {
+            case 0: emit_shell<0>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
+            case 1: emit_shell<1>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
+            case 2: emit_shell<2>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
+            default: emit_shell<3>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
             }
-            for (int m = 0; m < nm; m++, f++) {
-                if (f < f_lo || f >= f_hi) continue;
-                const int qi = R.l < 2 ? 0 : (R.l == 2 ? ci[m] - 2 : ci[m] - 5);
-                const df val = df_mul_f(rc[qi], Q[m]);
-                out[f * kPhiValStride] = make_float2(val.hi, val.lo);
-            }
+            f += nm;
         }
     }
 }
@@ -469,6 +486,7 @@ __global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch
     __shared__ unsigned int rowmax[2][128];          // |phi|, |w v phi| maxima (float bits)
     __shared__ float rowsum[2][128];                 // sums of |phi|, |w v phi| over the points
     __shared__ float fsc[2][128][2];                 // per row: scale, unit
+    __shared__ float wvf[kMaxBatchPoints];           // |w v| per point (FP32), first pass
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
     const TcBatch T = tb[it.batch];
@@ -482,63 +500,74 @@ __global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch
     uint8_t *phi_img = ws + T.img_phi;
     uint8_t *a_img = ws + T.img_aux;
     if (fixed) {
-        // pass 1: row maxima of |phi| and |w v phi| over the batch's points (FP32)
+        // pass 1: row maxima and sums of |phi| and |w v phi| over the batch's
+        // points (FP32).  One warp per (atom, shell) of the block; lanes stride
+        // over the points and keep per-function partials in registers.
         for (int q = threadIdx.x; q < 256; q += blockDim.x) {
-            (&rowmax[0][0])[q] = 0u;
+            (&rowmax[0][0])[q] = 0u;          // rows past n_b stay zero
             (&rowsum[0][0])[q] = 0.f;
         }
+        for (int p = threadIdx.x; p < B.np; p += blockDim.x)
+            wvf[p] = fminf(fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p])), 1.0e30f);
         __syncthreads();
-        const int units = ne * 64 * T.nc;
-        for (int u0 = 0; u0 < units; u0 += blockDim.x) {
-            const int u = u0 + threadIdx.x;
-            const bool in = u < units;
-            const int uu = in ? u : 0;
-            const int e = e0 + (uu >> 6) % ne, c = (uu >> 6) / ne, k = uu & 63, p = c * 64 + k;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+        int job = 0;
+        for (int e = e0; e <= e1; e++) {
             const DevAct A = act[e];
             const DevSpecies S = P.species[P.atom_species[A.atom]];
             const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
-            const bool live = in && p < B.np;
-            float x = 0.f, y = 0.f, z = 0.f, wvp = 0.f;
-            if (live) {
-                const float *pp = P.pts_dd + 6 * (B.pt0 + p);
-                const float *aa = P.atom_dd + 6 * A.atom;
-                x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
-                y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
-                z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
-                wvp = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p]));
-            }
-            const float d = sqrtf(x * x + y * y + z * z);
+            const float *aa = P.atom_dd + 6 * A.atom;
+            const float ax = aa[0] + aa[1], ay = aa[2] + aa[3], az = aa[4] + aa[5];
             int f = 0;
             for (int sh = 0; sh < S.n_shell; sh++) {
                 const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
                 const int nm = 2 * R.l + 1;
-                if (f + nm <= f_lo || f >= f_hi) {
-                    f += nm;
-                    continue;
+                const int f1 = f;
+                f += nm;
+                if (f <= f_lo || f1 >= f_hi) continue;
+                if ((job++ % nwarp) != warp) continue;
+                float mx[7], sm[7], mxw[7], smw[7];
+#pragma unroll
+                for (int m = 0; m < 7; m++) mx[m] = sm[m] = mxw[m] = smw[m] = 0.f;
+                for (int p = lane; p < B.np; p += 32) {
+                    const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                    const float x = (pp[0] + pp[1]) - ax, y = (pp[2] + pp[3]) - ay, z = (pp[4] + pp[5]) - az;
+                    const float d = sqrtf(x * x + y * y + z * z);
+                    const float rad = radial_over_d_f32(R, P.coef_dd, d);
+                    if (rad == 0.f) continue;
+                    float Q[7];
+                    int ci[7];
+                    ylm_poly_f32(R.l, x, y, z, Q, ci);
+                    const float wvp = wvf[p];
+#pragma unroll
+                    for (int m = 0; m < 7; m++) {
+                        if (m >= nm) break;
+                        const float a = fminf(fabsf(rad * kYlmC[ci[m]].x * Q[m]), 1.0e30f);
+                        const float aw = fminf(a * wvp, 1.0e30f);
+                        mx[m] = fmaxf(mx[m], a);
+                        sm[m] += a;
+                        mxw[m] = fmaxf(mxw[m], aw);
+                        smw[m] += aw;
+                    }
                 }
-                const float rad = live ? radial_over_d_f32(R, P.coef_dd, d) : 0.f;
-                float Q[7];
-                int ci[7];
-                ylm_poly_f32(R.l, x, y, z, Q, ci);
-                for (int m = 0; m < nm; m++, f++) {
-                    float a = fabsf(rad * kYlmC[ci[m]].x * Q[m]);
-                    if (!(a < 1.0e30f)) a = 1.0e30f;           // non-finite input: keep the scale finite
-                    const float aw = fminf(a * wvp, 1.0e30f);
-                    unsigned int mp = __float_as_uint(a), ma = __float_as_uint(aw);
-                    float sp = a, sa = aw;
-                    // a warp holds 32 consecutive points of one atom and chunk
-                    mp = __reduce_max_sync(0xffffffffu, mp);
-                    ma = __reduce_max_sync(0xffffffffu, ma);
+#pragma unroll
+                for (int m = 0; m < 7; m++) {
+                    if (m >= nm) break;
+                    unsigned int a = __reduce_max_sync(0xffffffffu, __float_as_uint(mx[m]));
+                    unsigned int aw = __reduce_max_sync(0xffffffffu, __float_as_uint(mxw[m]));
+                    float s1 = sm[m], s2 = smw[m];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        sp += __shfl_xor_sync(0xffffffffu, sp, o);
-                        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
                     }
-                    if ((threadIdx.x & 31) == 0 && f >= f_lo && f < f_hi) {
-                        atomicMax(&rowmax[0][A.fn_loc + f - r0], mp);
-                        atomicMax(&rowmax[1][A.fn_loc + f - r0], ma);
-                        atomicAdd(&rowsum[0][A.fn_loc + f - r0], sp);
-                        atomicAdd(&rowsum[1][A.fn_loc + f - r0], sa);
+                    const int fr = f1 + m;
+                    if (lane == 0 && fr >= f_lo && fr < f_hi) {
+                        const int row = A.fn_loc + fr - r0;
+                        rowmax[0][row] = a;
+                        rowmax[1][row] = aw;
+                        rowsum[0][row] = s1;
+                        rowsum[1][row] = s2;
                     }
                 }
             }
@@ -553,7 +582,7 @@ __global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch
         }
         __syncthreads();
     }
-    for (int c2 = 0; c2 < 2 * T.nc_alloc; c2++) {
+    for (int c2 = 0; c2 < 2 * T.nc; c2++) {
         const int c = c2 >> 1, half = c2 & 1;
         eval_block_chunk(P, B, act, e0, ne, r0, c * 64 + half * 32, phi_smem);
         if (threadIdx.x < 32) {
@@ -640,7 +669,9 @@ __global__ void __launch_bounds__(kPhiThreads) k_tc_phi_cols(DevPlan P, const Tc
                 float Q[7];
                 int ci[7];
                 ylm_poly_f32(R.l, x, y, z, Q, ci);
-                for (int m = 0; m < 2 * R.l + 1; m++) {
+#pragma unroll
+                for (int m = 0; m < 7; m++) {
+                    if (m >= 2 * R.l + 1) break;
                     const float a = fabsf(rad * kYlmC[ci[m]].x * Q[m]);
                     mx = fmaxf(mx, a);
                     sm += a;
@@ -1025,7 +1056,10 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
         rsc[1][threadIdx.x] = un;
     }
     uint8_t *img = ws + T.img_aux;
-    for (int kc = 0; kc < T.nkc; kc++) {
+    // D is symmetric: block row J holds only the chunks i >= 128 J, the
+    // diagonal block halved (n = 2 sum_J phi_J . E_J, exact in binary)
+    for (int kc = 2 * J; kc < T.nkc; kc++) {
+        const float blk = kc < 2 * J + 2 ? 0.5f : 1.f;
         __syncthreads();
         if (threadIdx.x < 64) {
             const int i = kc * 64 + threadIdx.x;
@@ -1071,7 +1105,7 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
                 else
                     k = ci.atom > rj.atom ? off + ci.gi : ci.rp - ci.li + off;
                 const float2 v = __ldg(ddv + k);
-                const float sc = i == j ? 1.f : offdiag_scale;
+                const float sc = (i == j ? 1.f : offdiag_scale) * blk;
                 x[q] = df{v.x * sc, v.y * sc};
             }
             uint8_t *dst = img + unit_offset(J, T.nkc, kc, r, g);
@@ -1085,7 +1119,9 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
 
 // ------------------------------------------------- density on tcgen05 (K3b)
 // Persistent: one CTA per SM walks the items (batch, 128-point tile m); for
-// each 128-function block J of the batch, E^T[j][p] = sum_i D[j][i] phi_i(p)
+// each 128-function block J of the batch, E^T[j][p] = sum_{i >= 128 J} D'[j][i] phi_i(p)
+// over the upper block triangle of the symmetric D (D' = D with its diagonal
+// block halved; n_p = 2 sum_j E^T[j][p] phi_j(p))
 // (A = D image, K-major; B = phi image read as MN-major) accumulates in one
 // of two tensor-memory sets while warps 0-3 finish the previous block:
 // n_p += sum_j E^T[j][p] phi_j(p) in double-float, lane j multiplying by its
@@ -1121,7 +1157,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                 const int m = it.ti;
                 const uint8_t *d_img = ws + T.img_aux, *phi_img = ws + T.img_phi;
                 for (int J = 0; J < T.nrb && ok; J++) {
-                    for (int kc = 0; kc < T.nkc; kc++, n++) {
+                    for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
                         const int st = (int)(n % kStages);
                         const long long use = n / kStages;
                         if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
@@ -1164,7 +1200,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     }
                     tc_fence_after();
                     bool started[2] = {false, false};
-                    for (int kc = 0; kc < T.nkc; kc++, n++) {
+                    for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
                         const int st = (int)(n % kStages);
                         if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
                             ok = false;
@@ -1284,8 +1320,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
             if (threadIdx.x < 128) {
                 const int p = m * 128 + threadIdx.x;
                 if (ok && p < B.np)
-                    n_out[B.pt0 + p] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
-                                       red[3][threadIdx.x];
+                    n_out[B.pt0 + p] = 2.0 * (red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
+                                              red[3][threadIdx.x]);
             }
             epi_sync();
             for (int cq = 0; cq < 2; cq++) red[quad][(2 * half + cq) * 32 + lane] = 0.0;
@@ -1429,33 +1465,34 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
     }
     close_wave(n_sb);
     for (TcWave &wv : t.waves) {
-        auto live = [&](int b) { return t.sb[b].np > 0 && t.sb[b].nfn > 0; };
-        wv.phi0 = (long long)t.items.size();
+        // longest first: the wave's batches by contraction cost P n^2, each
+        // batch's items kept together (they share image tiles in L2); the
+        // persistent kernels stride over this list, so the small items land last
+        std::vector<int> ord;
         for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
-            if (live(b))
-                for (int I = 0; I < t.batches[b].nrb; I++) t.items.push_back(WorkItem{b, (short)I, 0});
+            if (t.sb[b].np > 0 && t.sb[b].nfn > 0) ord.push_back(b);
+        auto cost = [&](int b) { return (double)t.sb[b].np * t.sb[b].nfn * t.sb[b].nfn; };
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        wv.phi0 = (long long)t.items.size();
+        for (int b : ord)
+            for (int I = 0; I < t.batches[b].nrb; I++) t.items.push_back(WorkItem{b, (short)I, 0});
         wv.nphi = (long long)t.items.size() - wv.phi0;
         wv.h0 = (long long)t.items.size();
-        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
-            if (live(b))
-                for (int I = 0; I < t.batches[b].nrb; I++)
-                    for (int J = I; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)I, (short)J});
+        for (int b : ord)
+            for (int I = 0; I < t.batches[b].nrb; I++)
+                for (int J = I; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)I, (short)J});
         wv.nh = (long long)t.items.size() - wv.h0;
         wv.g0 = (long long)t.items.size();
-        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
-            if (live(b))
-                for (int J = 0; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)J, 0});
+        for (int b : ord)
+            for (int J = 0; J < t.batches[b].nrb; J++) t.items.push_back(WorkItem{b, (short)J, 0});
         wv.ng = (long long)t.items.size() - wv.g0;
         wv.pc0 = (long long)t.items.size();
-        for (int b = wv.b0; b < wv.b0 + wv.nb; b++)
-            if (live(b))
-                for (int c = 0; c < t.batches[b].nc_alloc; c++) t.items.push_back(WorkItem{b, (short)c, 0});
+        for (int b : ord)
+            for (int c = 0; c < t.batches[b].nc_alloc; c++) t.items.push_back(WorkItem{b, (short)c, 0});
         wv.npc = (long long)t.items.size() - wv.pc0;
         wv.d0 = (long long)t.items.size();
-        for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
-            if (!live(b)) continue;
+        for (int b : ord)
             for (int mt = 0; mt < t.batches[b].nc_alloc / 2; mt++) t.items.push_back(WorkItem{b, (short)mt, 0});
-        }
         wv.nd = (long long)t.items.size() - wv.d0;
         for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
             const double P = t.sb[b].np, n = t.sb[b].nfn;
@@ -1463,9 +1500,10 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
             wv.phi_bytes += 32.0 * P + 12.0 * P * n;
             wv.h_flops += P * n * (n + 1.0);
             wv.h_bytes += 16.0 * n * (n + 1) / 2 + 12.0 * P * n;
-            wv.n_flops += 2.0 * P * n * n + 2.0 * P * n;
-            wv.n_bytes += 6.0 * n * n + 6.0 * P * n + 16.0 * P;
-            wv.g_bytes += 8.0 * n * n + 6.0 * n * n;
+            // symmetric D: the upper block triangle (about half of n^2)
+            wv.n_flops += P * n * (n + 1.0) + 2.0 * P * n;
+            wv.n_bytes += 3.0 * n * n + 6.0 * P * n + 16.0 * P;
+            wv.g_bytes += 7.0 * n * n;
         }
     }
     // scratch before the images: the fixed-point H accumulator, or the

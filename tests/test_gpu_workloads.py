@@ -108,8 +108,14 @@ def test_many_molecules_in_one_plan(fgi, precision, tol):
         r, c = rows_cols(ctx, s)
         assert np.max(np.abs(h[val0:val0 + nnz] - H[r, c])) <= tol * max(1.0, np.abs(H).max())
         nref = O.density(B, prob.pts[pts], Ds[s])
-        assert np.linalg.norm(n[pts] - nref) / np.linalg.norm(nref) <= max(tol, 1e-12) * 10
-        assert tr[s] == pytest.approx(float(np.sum(prob.w[pts] * nref)), rel=1e-6, abs=1e-9)
+        rel_n = max(tol, 1e-12) * 10
+        assert np.linalg.norm(n[pts] - nref) / np.linalg.norm(nref) <= rel_n
+        # the trace is sum_p w_p n_p in FP64: by Cauchy-Schwarz its error is at
+        # most ||w|| ||n - nref|| (a random D gives a sign-changing n, so the
+        # trace itself may be small against that bound)
+        tr_ref = float(np.sum(prob.w[pts] * nref))
+        bound = rel_n * np.linalg.norm(prob.w[pts]) * np.linalg.norm(nref) + 1e-12 * np.sum(np.abs(prob.w[pts] * nref))
+        assert abs(tr[s] - tr_ref) <= bound, (tr[s], tr_ref, bound)
 
 
 def test_split_step_replays_as_a_cuda_graph(fgi):
