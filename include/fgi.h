@@ -132,6 +132,16 @@ int fgi_get_sizes(fgi_ctx *ctx, int64_t *n_fn, int64_t *nnz, int64_t *n_pts, int
 int fgi_get_system(fgi_ctx *ctx, int sys, int64_t *fn0, int64_t *n_fn, int64_t *val0,
                    int64_t *nnz);
 
+/* Per-batch work after fgi_plan (host arrays of n_batch entries, written by
+   the library): points P_b and active functions n_b of every batch, in the
+   order fgi_set_grid gave the batches.  The contractions cost about
+   P_b n_b^2; a caller that distributes one system over several processes
+   (the paper's process-first parallelisation, "Meeting the Exascale
+   Challenges") splits the batches across ranks by this cost.  Either
+   pointer may be NULL.  The paper has no counterpart for the call itself.
+   FGI_ERR_ARG if n_batch differs from the planned batch count. */
+int fgi_get_batch_work(fgi_ctx *ctx, int64_t n_batch, int64_t *points, int32_t *n_active_fns);
+
 /* CSR pattern of system `sys` (host arrays owned by the context, valid until
    the next fgi_plan/fgi_set_*): rowptr[n_fn(sys)+1] (relative to val0(sys))
    and col[nnz(sys)] (function index within the system). */

@@ -887,6 +887,20 @@ int fgi_get_system(fgi_ctx *c, int sys, int64_t *fn0, int64_t *n_fn, int64_t *va
     return FGI_OK;
 }
 
+int fgi_get_batch_work(fgi_ctx *c, int64_t n_batch, int64_t *points, int32_t *n_active_fns)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (n_batch != (int64_t)c->batches_f64.size())
+        return set_err(c, FGI_ERR_ARG, "n_batch %lld differs from the planned %lld batches", (long long)n_batch,
+                       (long long)c->batches_f64.size());
+    for (int64_t b = 0; b < n_batch; b++) {
+        if (points) points[b] = c->batches_f64[b].np;
+        if (n_active_fns) n_active_fns[b] = c->batches_f64[b].nfn;
+    }
+    return FGI_OK;
+}
+
 int fgi_get_pattern(fgi_ctx *c, int sys, int64_t *nnz, const int64_t **rowptr, const int **col)
 {
     int rc = check_ready(c);

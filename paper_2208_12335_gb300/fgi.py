@@ -27,7 +27,7 @@ SYMBOLS = ["fgi_create", "fgi_destroy", "fgi_last_error", "fgi_add_radial", "fgi
            "fgi_set_systems", "fgi_set_grid", "fgi_plan", "fgi_set_precision", "fgi_get_sizes",
            "fgi_get_system", "fgi_get_pattern", "fgi_workspace_size", "fgi_integrate_h",
            "fgi_density", "fgi_adjoint", "fgi_trace", "fgi_sync", "fgi_profile",
-           "fgi_profile_read", "fgi_integrate_h_static"]
+           "fgi_profile_read", "fgi_integrate_h_static", "fgi_get_batch_work"]
 KERNEL_KINDS = {"basis": 0, "h": 1, "density": 2, "adjoint": 3, "other": 4}
 
 
@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgi_profile": ([P, I], I),
         "fgi_profile_read": ([P, I, C.POINTER(I64), C.POINTER(D), C.POINTER(D), C.POINTER(D)], I),
         "fgi_integrate_h_static": ([P, P, P, I, P], I),
+        "fgi_get_batch_work": ([P, I64, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +168,7 @@ class Context:
         batch_sys = _np(batch_sys, np.int32)
         self._check(self._lib.fgi_set_grid(self._h, len(w), _ptr(xyz), _ptr(w), len(batch_off) - 1,
                                            _ptr(batch_off), _ptr(batch_sys)))
+        self._n_batch = len(batch_off) - 1
 
     def plan(self, precision="fp64", tune_path=None):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -197,6 +199,14 @@ class Context:
         v = [C.c_int64() for _ in range(4)]
         self._check(self._lib.fgi_get_system(self._h, s, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)       # fn0, n_fn, val0, nnz
+
+    def batch_work(self):
+        """Per batch: points P_b (int64) and active functions n_b (int32)."""
+        nb = getattr(self, "_n_batch", 0)
+        pts = np.zeros(nb, np.int64)
+        nfn = np.zeros(nb, np.int32)
+        self._check(self._lib.fgi_get_batch_work(self._h, nb, _ptr(pts), _ptr(nfn)))
+        return pts, nfn
 
     def pattern(self, s: int = 0):
         nnz = C.c_int64()

@@ -176,3 +176,22 @@ def test_empty_batches_and_far_points_plan(fgi):
                       np.concatenate([prob.v, [0.0, 0.0]]))
     ctx = host_ctx(fgi, prob2)
     assert ctx.sizes()[2] == prob.n_pts + 2
+
+
+def test_batch_work_counts_points_and_covers_the_nonzero_functions(fgi):
+    import oracle as O
+    prob = W.si64()
+    ids = np.arange(0, prob.n_batch, max(1, prob.n_batch // 12))
+    sub = prob.subgrid(ids)
+    ctx = host_ctx(fgi, sub)
+    pts, nfn = ctx.batch_work()
+    assert np.array_equal(pts, np.diff(sub.batch_off))
+    B = O.system_basis(sub)
+    for b in range(sub.n_batch):
+        p = sub.pts[sub.batch_off[b]:sub.batch_off[b + 1]]
+        need = len(O.active_functions(B, p))
+        # the plan's active set is a superset (bounding-sphere test), whole atoms
+        assert need <= nfn[b] <= B.n_fn
+    with pytest.raises(fgi.FGIError) as e:
+        ctx._check(ctx._lib.fgi_get_batch_work(ctx._h, sub.n_batch + 1, None, None))
+    assert e.value.code == -1
