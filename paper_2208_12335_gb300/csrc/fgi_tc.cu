@@ -747,12 +747,14 @@ __global__ void k_fix_to_h(const long long *acc, double *h, long long n, int acc
 // ----------------------------------------------- H contraction on tcgen05 (K2)
 // Persistent: one CTA per SM walks the tile list (batch, I, J), I <= J, with
 // stride gridDim.x; each tile is 128 x 128 outputs with K = the batch's
-// points in chunks of 64.  Warp 4 (one lane) streams operand chunks into a
-// two-stage shared-memory ring with bulk copies; warp 5 (one lane) issues
-// the MMAs into one of two tensor-memory accumulator sets (acc0 + acc1,
-// 256 columns each); warps 0-3 drain the other set (TMEM lanes 32w..32w+31)
-// and scatter the upper triangle into the fixed-point H accumulator, so the
-// scatter of one tile overlaps the MMAs of the next.
+// points in chunks of 64, computed transposed (A = phi of block J, B = w v phi
+// of block I).  Warp 8 (one lane) streams operand chunks into a two-stage
+// shared-memory ring with bulk copies; warp 9 (one lane) issues the MMAs
+// into one of two tensor-memory accumulator sets (acc0 + acc1, 256 columns
+// each); warps 0-7 drain the other set and scatter the upper triangle into
+// the fixed-point H accumulator, so the scatter of one tile overlaps the
+// MMAs of the next.  A warp's lanes hold 32 consecutive functions j, so the
+// atomics for one column i land on consecutive values of row i.
 constexpr int kThreadsTc = 320;                  // warps 0-7 epilogue, 8 producer, 9 MMA
 constexpr int kWarpProducer = 8, kWarpMma = 9;
 constexpr int kEpiThreads = 256;
@@ -763,10 +765,9 @@ constexpr int kStageBytes = 6 * kChunkBytes;     // A and B operands, 3 planes e
 #endif
 constexpr int kDensityOrder = FGI_DENSITY_ORDER;  // split products kept in the density (6 of 9)
 
-struct ColRef {                                  // compact column reference for the H scatter
-    int gi;                                      // global function
+struct ColRef {                                  // column i of an H tile (a row of the stored triangle)
+    long long rpl;                               // first stored value of row i minus i's index in its atom
     int atom;                                    // global atom
-    int li;                                      // index inside the atom
     int loc;                                     // atom index inside its system
 };
 
@@ -849,7 +850,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
             for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
                 const WorkItem it = items[t];
                 const TcBatch T = tb[it.batch];
-                const uint8_t *a_img = ws + T.img_aux, *b_img = ws + T.img_phi;
+                // A = phi rows of block J (TMEM lanes), B = w v phi rows of block I
+                // (TMEM columns): the transposed tile, so that the scatter of one
+                // column i by the 32 lanes of a warp hits consecutive values of row i
+                const uint8_t *a_img = ws + T.img_phi, *b_img = ws + T.img_aux;
                 for (int c = 0; c < T.nc; c++, n++) {
                     const int st = (int)(n % kStages);
                     const long long use = n / kStages;
@@ -861,10 +865,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     mbar_expect_tx(&S->full[st], 2 * chunk);
                     for (int s = 0; s < n_split; s++) {
                         bulk_g2s(a_sm + s * kChunkBytes,
-                                 a_img + s * T.plane_phi + (long long)(it.ti * T.nc_alloc + c) * kChunkBytes,
+                                 a_img + s * T.plane_phi + (long long)(it.tj * T.nc_alloc + c) * kChunkBytes,
                                  kChunkBytes, &S->full[st]);
                         bulk_g2s(b_sm + s * kChunkBytes,
-                                 b_img + s * T.plane_phi + (long long)(it.tj * T.nc_alloc + c) * kChunkBytes,
+                                 b_img + s * T.plane_phi + (long long)(it.ti * T.nc_alloc + c) * kChunkBytes,
                                  kChunkBytes, &S->full[st]);
                     }
                 }
@@ -905,7 +909,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
         }
         __syncwarp();
     } else {
-        // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 64 (w / 4) .. + 63
+        // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 (functions j of block J),
+        // columns 64 (w / 4) .. + 63 (functions i of block I)
         int lt = 0;
         bool bad = false;
         const int quad = warp & 3, half = warp >> 2;
@@ -917,54 +922,55 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
             const int buf = lt & 1, use = lt >> 1;
             const int i0 = it.ti * 128, j0 = it.tj * 128;
             if (threadIdx.x < 128) {
-                const int j = j0 + threadIdx.x;
-                if (j < B.nfn) {
-                    const FnRef c = fn_ref(P, act, find_act(act, B.n_act, j), j);
-                    S->ref[buf][threadIdx.x] = ColRef{(int)c.gi, c.atom, c.li, c.loc};
+                const int i = i0 + threadIdx.x;
+                if (i < B.nfn) {
+                    const FnRef c = fn_ref(P, act, find_act(act, B.n_act, i), i);
+                    S->ref[buf][threadIdx.x] = ColRef{c.rp - c.li, c.atom, c.loc};
                 }
             }
             const int r = quad * 32 + lane;
-            const int i = i0 + r;
-            FnRef rref{};
-            if (i < B.nfn) rref = fn_ref(P, act, find_act(act, B.n_act, i), i);
-            const int *pp_row = P.pairpos + P.sys_pair_off[B.sys] + (long long)rref.loc * P.sys_nat[B.sys];
+            const int j = j0 + r;                  // this lane's function (block J)
+            FnRef jref{};
+            if (j < B.nfn) jref = fn_ref(P, act, find_act(act, B.n_act, j), j);
+            const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
+            const int nat = P.sys_nat[B.sys];
             epi_sync();
             const bool ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
             tc_fence_after();
             const uint32_t acc_base = tmem + buf * 256 + lane_base;
             for (int cq = 0; cq < 2; cq++) {
                 const int cc = 2 * half + cq;
-                if (j0 + cc * 32 >= B.nfn) break;
+                if (i0 + cc * 32 >= B.nfn) break;
                 float a0[32], a1[32];
                 tmem_ld32(acc_base + cc * 32, a0);
                 if (n_split > 1) tmem_ld32(acc_base + 128 + cc * 32, a1);
                 tmem_wait_ld();
-                if (!ok || i >= B.nfn) continue;
-                // stored value of (i, j) = base(atom of j) + gj along a run of one atom
+                if (!ok || j >= B.nfn) continue;
+                // stored value of (i, j), i <= j: row i, (rp_i - li) + [pair offset of
+                // atom(j) in row i, 0 for the same atom] + lj
                 int cur_atom = -1;
-                long long base = 0;           // may be negative: k = base + gj
+                int ppv = 0;
                 bool stored = false;
 #pragma unroll
                 for (int q = 0; q < 32; q++) {
-                    const int jl = cc * 32 + q;
-                    const int j = j0 + jl;
-                    if (j >= B.nfn || i > j) continue;
-                    const ColRef cj = S->ref[buf][jl];
-                    if (cj.atom != cur_atom) {
-                        cur_atom = cj.atom;
-                        if (cj.atom == rref.atom) {
-                            base = rref.rp - rref.gi;
+                    const int il = cc * 32 + q;
+                    const int i = i0 + il;
+                    if (i >= B.nfn || i > j) continue;
+                    const ColRef ci = S->ref[buf][il];
+                    if (ci.atom != cur_atom) {
+                        cur_atom = ci.atom;
+                        if (ci.atom == jref.atom) {
+                            ppv = 0;
                             stored = true;
                         } else {
-                            const int pp = __ldg(pp_row + cj.loc);
-                            stored = pp >= 0;
-                            base = rref.rp + pp - rref.li - (cj.gi - cj.li);
+                            ppv = __ldg(pp_sys + (long long)ci.loc * nat + jref.loc);
+                            stored = ppv >= 0;
                         }
                     }
                     if (!stored) continue;
                     long long fx = f32_to_fix(a0[q], bad);
                     if (n_split > 1) fx += f32_to_fix(a1[q], bad);
-                    if (fx != 0) atomicAdd(hfix + base + cj.gi, (unsigned long long)fx);
+                    if (fx != 0) atomicAdd(hfix + ci.rpl + ppv + jref.li, (unsigned long long)fx);
                 }
             }
             tc_fence_before();
@@ -1118,16 +1124,19 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
 }
 
 // ------------------------------------------------- density on tcgen05 (K3b)
-// Persistent: one CTA per SM walks the items (batch, 128-point tile m); for
-// each 128-function block J of the batch, E^T[j][p] = sum_{i >= 128 J} D'[j][i] phi_i(p)
-// over the upper block triangle of the symmetric D (D' = D with its diagonal
-// block halved; n_p = 2 sum_j E^T[j][p] phi_j(p))
-// (A = D image, K-major; B = phi image read as MN-major) accumulates in one
-// of two tensor-memory sets while warps 0-3 finish the previous block:
-// n_p += sum_j E^T[j][p] phi_j(p) in double-float, lane j multiplying by its
-// own phi row and the warp reducing over j.
+// Persistent: one CTA per SM walks the items (batch, 128-point tile m,
+// 128-function block J), J ascending so the longest contractions come first:
+// E^T[j][p] = sum_{i >= 128 J} D'[j][i] phi_i(p) over the upper block
+// triangle of the symmetric D (D' = D with its diagonal block halved;
+// A = D image, K-major; B = phi image read as MN-major) accumulates in one of
+// two tensor-memory sets while warps 0-7 finish the previous item: the
+// partial density sum_{j in J} E^T[j][p] phi_j(p) in double-float (lane j
+// multiplies by its own phi row, the warp reduces over j), one row of 128
+// doubles per item.  Many items per batch keep the CTAs on few batches at a
+// time, so the D and phi images are read from L2.  k_density_sum then forms
+// n_p = 2 sum_J partial_J(p).
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                              int n_items, const uint8_t *ws, double *n_out,
+                                                              int n_items, const uint8_t *ws, double *part,
                                                               int n_split)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -1135,7 +1144,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
     TcRing *S = reinterpret_cast<TcRing *>(sm + kStages * kStageBytes);
     __shared__ double red[4][128];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) (&red[0][0])[k] = 0.0;
     if (threadIdx.x == 0) ring_init(S);
     if (warp == kWarpMma) {
         tmem_alloc(&S->tmem, 512);
@@ -1154,29 +1162,27 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
             for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
                 const WorkItem it = items[t];
                 const TcBatch T = tb[it.batch];
-                const int m = it.ti;
+                const int m = it.ti, J = it.tj;
                 const uint8_t *d_img = ws + T.img_aux, *phi_img = ws + T.img_phi;
-                for (int J = 0; J < T.nrb && ok; J++) {
-                    for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
-                        const int st = (int)(n % kStages);
-                        const long long use = n / kStages;
-                        if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
-                            ok = false;
-                            break;
-                        }
-                        uint8_t *a_sm = sm + st * kStageBytes, *b_sm = a_sm + 3 * kChunkBytes;
-                        mbar_expect_tx(&S->full[st], 2 * chunk);
-                        const int I = kc >> 1, half = kc & 1;
-                        for (int s = 0; s < n_split; s++) {
-                            bulk_g2s(a_sm + s * kChunkBytes,
-                                     d_img + s * T.plane_d + (long long)(J * T.nkc + kc) * kChunkBytes, kChunkBytes,
-                                     &S->full[st]);
-                            for (int c2 = 0; c2 < 2; c2++)
-                                bulk_g2s(b_sm + s * kChunkBytes + c2 * 8192,
-                                         phi_img + s * T.plane_phi +
-                                             ((long long)(I * T.nc_alloc + 2 * m + c2) * 16 + 8 * half) * 1024,
-                                         8192, &S->full[st]);
-                        }
+                for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
+                    const int st = (int)(n % kStages);
+                    const long long use = n / kStages;
+                    if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *a_sm = sm + st * kStageBytes, *b_sm = a_sm + 3 * kChunkBytes;
+                    mbar_expect_tx(&S->full[st], 2 * chunk);
+                    const int I = kc >> 1, half = kc & 1;
+                    for (int s = 0; s < n_split; s++) {
+                        bulk_g2s(a_sm + s * kChunkBytes,
+                                 d_img + s * T.plane_d + (long long)(J * T.nkc + kc) * kChunkBytes, kChunkBytes,
+                                 &S->full[st]);
+                        for (int c2 = 0; c2 < 2; c2++)
+                            bulk_g2s(b_sm + s * kChunkBytes + c2 * 8192,
+                                     phi_img + s * T.plane_phi +
+                                         ((long long)(I * T.nc_alloc + 2 * m + c2) * 16 + 8 * half) * 1024,
+                                     8192, &S->full[st]);
                     }
                 }
             }
@@ -1190,30 +1196,30 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
             long long n = 0;
             int u = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x) {
-                const TcBatch T = tb[items[t].batch];
-                for (int J = 0; J < T.nrb && ok; J++, u++) {
-                    const int buf = u & 1, use = u >> 1;
-                    if (use > 0 && !mbar_wait_a(&S->tempty[buf], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
+            for (int t = blockIdx.x; t < n_items && ok; t += gridDim.x, u++) {
+                const WorkItem it = items[t];
+                const TcBatch T = tb[it.batch];
+                const int J = it.tj;
+                const int buf = u & 1, use = u >> 1;
+                if (use > 0 && !mbar_wait_a(&S->tempty[buf], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                bool started[2] = {false, false};
+                for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
+                    const int st = (int)(n % kStages);
+                    if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    bool started[2] = {false, false};
-                    for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
-                        const int st = (int)(n % kStages);
-                        if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint8_t *a_sm = sm + st * kStageBytes;
-                        mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started,
-                                  kDensityOrder);
-                        tc_commit(&S->empty[st]);
-                    }
-                    tc_commit(&S->tfull[buf]);
+                    const uint8_t *a_sm = sm + st * kStageBytes;
+                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started,
+                              kDensityOrder);
+                    tc_commit(&S->empty[st]);
                 }
+                tc_commit(&S->tfull[buf]);
             }
         }
         __syncwarp();
@@ -1224,47 +1230,46 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         int u = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
+        for (int t = blockIdx.x; t < n_items; t += gridDim.x, u++) {
             const WorkItem it = items[t];
             const DevBatch B = P.batches[it.batch];
             const TcBatch T = tb[it.batch];
-            const int m = it.ti;
+            const int m = it.ti, J = it.tj;
             const uint8_t *phi_img = ws + T.img_phi;
-            for (int J = 0; J < T.nrb; J++, u++) {
-                const int buf = u & 1, use = u >> 1;
-                const int r = quad * 32 + lane;
-                const int j = J * 128 + r;
-                // this warp's phi rows for the first of its two column chunks: issued
-                // before the wait so the loads overlap the MMAs
-                uint4 pre[3][4];
-                {
-                    const int cc = 2 * half, c = 2 * m + (cc >> 1);
+            const int buf = u & 1, use = u >> 1;
+            const int r = quad * 32 + lane;
+            const int j = J * 128 + r;
+            // this warp's phi rows for the first of its two column chunks: issued
+            // before the wait so the loads overlap the MMAs
+            uint4 pre[3][4];
+            {
+                const int cc = 2 * half, c = 2 * m + (cc >> 1);
 #pragma unroll
-                    for (int gg = 0; gg < 4; gg++) {
-                        const long long off = unit_offset(J, T.nc_alloc, c, r, (cc & 1) * 4 + gg);
+                for (int gg = 0; gg < 4; gg++) {
+                    const long long off = unit_offset(J, T.nc_alloc, c, r, (cc & 1) * 4 + gg);
 #pragma unroll
-                        for (int sp = 0; sp < 3; sp++)
-                            pre[sp][gg] = sp < n_split ? *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi)
-                                                       : make_uint4(0u, 0u, 0u, 0u);
-                    }
+                    for (int sp = 0; sp < 3; sp++)
+                        pre[sp][gg] = sp < n_split ? *reinterpret_cast<const uint4 *>(phi_img + off + sp * T.plane_phi)
+                                                   : make_uint4(0u, 0u, 0u, 0u);
                 }
-                ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
-                tc_fence_after();
-                const uint32_t acc_base = tmem + buf * 256 + lane_base;
-                for (int cq = 0; cq < 2; cq++) {
-                    const int cc = 2 * half + cq;
-                    float a0[32], a1[32];
-                    tmem_ld32(acc_base + cc * 32, a0);
-                    if (n_split > 1)
-                        tmem_ld32(acc_base + 128 + cc * 32, a1);
-                    else
+            }
+            ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
+            tc_fence_after();
+            const uint32_t acc_base = tmem + buf * 256 + lane_base;
+            for (int cq = 0; cq < 2; cq++) {
+                const int cc = 2 * half + cq;
+                float a0[32], a1[32];
+                tmem_ld32(acc_base + cc * 32, a0);
+                if (n_split > 1)
+                    tmem_ld32(acc_base + 128 + cc * 32, a1);
+                else
 #pragma unroll
-                        for (int q = 0; q < 32; q++) a1[q] = 0.f;
-                    tmem_wait_ld();
-                    if (cq == 1) {
-                        tc_fence_before();
-                        mbar_arrive(&S->tempty[buf]);     // accumulator set may be reused
-                    }
+                    for (int q = 0; q < 32; q++) a1[q] = 0.f;
+                tmem_wait_ld();
+                if (cq == 1) {
+                    tc_fence_before();
+                    mbar_arrive(&S->tempty[buf]);     // accumulator set may be reused
+                }
                 // E^T[j][p] phi_j(p) for the 32 points of this column chunk in
                 // double-float (FP32 pipe): e = acc0 + acc1, phi = sum of its planes
                 const int c = 2 * m + (cc >> 1);
@@ -1312,24 +1317,38 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                         a1[q] = sum.lo;
                     }
                 }
-                    red[quad][cc * 32 + lane] += (double)a0[0] + (double)a1[0];
-                }
+                red[quad][cc * 32 + lane] = (double)a0[0] + (double)a1[0];
             }
-            // item complete: n_p from the four warps' partial sums
+            // item complete: this block's partial density at the tile's 128 points
             epi_sync();
             if (threadIdx.x < 128) {
-                const int p = m * 128 + threadIdx.x;
-                if (ok && p < B.np)
-                    n_out[B.pt0 + p] = 2.0 * (red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] +
-                                              red[3][threadIdx.x]);
+                const long long row = T.part0 + (long long)J * (T.nc_alloc / 2) + m;
+                part[row * 128 + threadIdx.x] =
+                    ok ? (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x])
+                       : 0.0;
             }
             epi_sync();
-            for (int cq = 0; cq < 2; cq++) red[quad][(2 * half + cq) * 32 + lane] = 0.0;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == kWarpMma) tmem_dealloc(tmem, 512);
+}
+
+// n_p = 2 sum_J part[J][p] over the batch's function blocks, in J order
+// (deterministic); one CTA of 128 threads per (batch, point tile).
+__global__ void __launch_bounds__(128) k_density_sum(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                    const double *part, double *n_out)
+{
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int p = it.ti * 128 + threadIdx.x;
+    if (p >= B.np) return;
+    const long long nt = T.nc_alloc / 2;
+    double s = 0.0;
+    for (int J = 0; J < T.nrb; J++) s += part[(T.part0 + J * nt + it.ti) * 128 + threadIdx.x];
+    n_out[B.pt0 + p] = 2.0 * s;
 }
 
 // Dynamic shared memory of the tcgen05 kernels: the two-stage ring (about
@@ -1451,19 +1470,32 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         max_ws = std::max(max_ws, off);
         t.waves.push_back(w);
     };
+    // each wave: the batches' images, then their partial densities (one row
+    // of 128 doubles per (point tile, function block))
+    long long part = 0;
+    auto part_rows = [&](int b) { return (long long)(t.batches[b].nc_alloc / 2) * t.batches[b].nrb; };
+    auto finish_wave = [&](int b_end) {
+        w.part_off = (off + 1023) / 1024 * 1024;
+        off = w.part_off + (size_t)part * 128 * sizeof(double);
+        close_wave(b_end);
+    };
     for (int b = 0; b < n_sb; b++) {
-        if (b > w.b0 && off + foot[b] > cap) {
-            close_wave(b);
+        const size_t pb = (size_t)part_rows(b) * 128 * sizeof(double);
+        if (b > w.b0 && off + foot[b] + pb + (size_t)part * 1024 + 1024 > cap) {
+            finish_wave(b);
             w = TcWave{};
             w.b0 = b;
             off = 0;
+            part = 0;
         }
         TcBatch &T = t.batches[b];
         T.img_phi = (long long)off;
         T.img_aux = (long long)(off + 3 * (size_t)T.plane_phi);
+        T.part0 = part;
+        part += part_rows(b);
         off += foot[b];
     }
-    close_wave(n_sb);
+    finish_wave(n_sb);
     for (TcWave &wv : t.waves) {
         // longest first: the wave's batches by contraction cost P n^2, each
         // batch's items kept together (they share image tiles in L2); the
@@ -1494,6 +1526,13 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         for (int b : ord)
             for (int mt = 0; mt < t.batches[b].nc_alloc / 2; mt++) t.items.push_back(WorkItem{b, (short)mt, 0});
         wv.nd = (long long)t.items.size() - wv.d0;
+        // MMA items: J ascending (the longest contractions first), every point tile
+        wv.e0 = (long long)t.items.size();
+        for (int b : ord)
+            for (int J = 0; J < t.batches[b].nrb; J++)
+                for (int mt = 0; mt < t.batches[b].nc_alloc / 2; mt++)
+                    t.items.push_back(WorkItem{b, (short)mt, (short)J});
+        wv.ne = (long long)t.items.size() - wv.e0;
         for (int b = wv.b0; b < wv.b0 + wv.nb; b++) {
             const double P = t.sb[b].np, n = t.sb[b].nfn;
             wv.phi_flops += 30.0 * P * n;
@@ -1634,9 +1673,13 @@ cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w
                               int n_split, cudaStream_t s)
 {
     if (w.nd <= 0) return cudaSuccess;
-    const int grid = (int)std::min<long long>(w.nd, t.num_sms);
-    k_tc_density<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.d0, (int)w.nd,
-                                                      (const uint8_t *)ws + t.img_base, n, n_split);
+    double *part = reinterpret_cast<double *>((uint8_t *)const_cast<void *>(ws) + t.img_base + w.part_off);
+    const int grid = (int)std::min<long long>(w.ne, t.num_sms);
+    k_tc_density<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.e0, (int)w.ne,
+                                                      (const uint8_t *)ws + t.img_base, part, n_split);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_density_sum<<<(unsigned)w.nd, 128, 0, s>>>(P, t.d_batches, t.d_items + w.d0, part, n);
     return cudaGetLastError();
 }
 

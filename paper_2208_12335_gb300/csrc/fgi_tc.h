@@ -27,6 +27,7 @@ struct TcBatch {
     int nc;                // 64-point chunks holding points
     int nc_alloc;          // allocated 64-point chunks (even)
     int nkc;               // 64-function chunks (density contraction depth)
+    long long part0;       // first partial-density row of the batch in its wave (128 doubles each)
 };
 
 struct TcWave {
@@ -35,7 +36,9 @@ struct TcWave {
     long long h0 = 0, nh = 0;        // items: (batch, I, J), I <= J
     long long g0 = 0, ng = 0;        // items: (batch, J) of the D gather
     long long pc0 = 0, npc = 0;      // items: (batch, 64-point chunk) of the density's phi image
-    long long d0 = 0, nd = 0;        // items: (batch, point tile of 128)
+    long long d0 = 0, nd = 0;        // items: (batch, point tile of 128): the final sums
+    long long e0 = 0, ne = 0;        // items: (batch, point tile, function block J) of the density MMA
+    size_t part_off = 0;             // workspace offset (after img_base) of the wave's partial densities
     double phi_flops = 0, phi_bytes = 0, h_flops = 0, h_bytes = 0, n_flops = 0, n_bytes = 0;
     double g_bytes = 0;
 };
