@@ -478,7 +478,7 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 
 constexpr int kPhiThreads = 256;
 
-__global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed)
 {
     extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kPhiThreads) k_tc_phi(DevPlan P, const TcBatch
 // density contracts over functions, so the fixed-point grid of the leading
 // term is per point (column): first the largest |phi_i(p)| over all of the
 // batch's functions (FP32), then every 128-row block in double-float.
-__global__ void __launch_bounds__(kPhiThreads) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                      uint8_t *ws, int n_split)
 {
     extern __shared__ float2 phi_smem[];
@@ -802,23 +802,32 @@ __device__ __forceinline__ void ring_init(TcRing *S)
     fence_mbar_init();
 }
 
-// issue the split products of one 64-deep chunk (4 k-steps of 16): every
-// product of combined order <= max_order except x2*y2; x0*y0 alone in
-// accumulator 0
+// Issue the split products of one 64-deep chunk (4 k-steps of 16): every
+// product of combined order <= ORDER except x2*y2; x0*y0 alone in
+// accumulator 0.  Fully unrolled with the descriptors of the stage computed
+// once: the plane and k-step offsets are added to the descriptors' address
+// field (addr >> 4, no carry out of it inside shared memory), so one lane
+// issues an MMA every few instructions and keeps the tensor pipe fed.
+// first: the chunk opens the item (the first product into each accumulator
+// overwrites it).
+template <int NSPLIT, int ORDER, bool B_MN>
 __device__ __forceinline__ void mma_chunk(uint32_t acc_base, const uint8_t *a_sm, const uint8_t *b_sm, uint32_t idesc,
-                                         int n_split, bool b_mn, bool *started, int max_order)
+                                          bool first)
 {
+    const uint64_t ad0 = desc_sw128(smem_u32(a_sm), 16, 1024);
+    const uint64_t bd0 = B_MN ? desc_sw128(smem_u32(b_sm), 8192, 1024) : desc_sw128(smem_u32(b_sm), 16, 1024);
 #pragma unroll
     for (int ks = 0; ks < 4; ks++) {
-        for (int pa = 0; pa < n_split; pa++) {
-            for (int pb = 0; pb < n_split; pb++) {
-                if (pa + pb > max_order || (pa == 2 && pb == 2)) continue;
+#pragma unroll
+        for (int pa = 0; pa < NSPLIT; pa++) {
+#pragma unroll
+            for (int pb = 0; pb < NSPLIT; pb++) {
+                if (pa + pb > ORDER || (pa == 2 && pb == 2)) continue;
                 const int acc = (pa + pb == 0) ? 0 : 1;
-                const uint64_t ad = desc_sw128(smem_u32(a_sm + pa * kChunkBytes + ks * 32), 16, 1024);
-                const uint64_t bd = b_mn ? desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 2048), 8192, 1024)
-                                         : desc_sw128(smem_u32(b_sm + pb * kChunkBytes + ks * 32), 16, 1024);
-                tc_mma(acc_base + acc * 128, ad, bd, idesc, started[acc] ? 1u : 0u);
-                started[acc] = true;
+                const uint64_t ad = ad0 + (uint64_t)((pa * kChunkBytes + ks * 32) >> 4);
+                const uint64_t bd = bd0 + (uint64_t)((pb * kChunkBytes + ks * (B_MN ? 2048 : 32)) >> 4);
+                const bool opens = ks == 0 && (acc == 0 || (pa == 0 && pb == 1));
+                tc_mma(acc_base + acc * 128, ad, bd, idesc, (first && opens) ? 0u : 1u);
             }
         }
     }
@@ -892,7 +901,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     break;
                 }
                 tc_fence_after();
-                bool started[2] = {false, false};
                 for (int c = 0; c < T.nc; c++, n++) {
                     const int st = (int)(n % kStages);
                     if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
@@ -901,7 +909,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     }
                     tc_fence_after();
                     const uint8_t *a_sm = sm + st * kStageBytes;
-                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, false, started, 3);
+                    if (n_split == 3)
+                        mma_chunk<3, 3, false>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, c == 0);
+                    else
+                        mma_chunk<1, 0, false>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, c == 0);
                     tc_commit(&S->empty[st]);
                 }
                 tc_commit(&S->tfull[buf]);
@@ -1206,7 +1217,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     break;
                 }
                 tc_fence_after();
-                bool started[2] = {false, false};
                 for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
                     const int st = (int)(n % kStages);
                     if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
@@ -1215,8 +1225,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     }
                     tc_fence_after();
                     const uint8_t *a_sm = sm + st * kStageBytes;
-                    mma_chunk(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, n_split, true, started,
-                              kDensityOrder);
+                    if (n_split == 3)
+                        mma_chunk<3, kDensityOrder, true>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc,
+                                                          kc == 2 * J);
+                    else
+                        mma_chunk<1, 0, true>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, kc == 2 * J);
                     tc_commit(&S->empty[st]);
                 }
                 tc_commit(&S->tfull[buf]);
