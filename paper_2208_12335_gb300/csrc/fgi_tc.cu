@@ -270,10 +270,12 @@ __device__ __forceinline__ void split_fixed(df x, float scale, float unit, __nv_
                                             __nv_bfloat16 &b, __nv_bfloat16 &c)
 {
     const float x0 = rintf(x.hi * scale) * unit;
-    const df r = df_two_sum(x.hi - x0, x.lo);
+    // x.hi - x0 is exact: x0 is a multiple of unit, and unit >= ulp(x.hi)
+    // because |x.hi| <= 2^e (1 + 2^-12) and unit = 2^(e - bits), bits <= 8
+    const float d = x.hi - x0;
     a = __float2bfloat16_rn(x0);
-    b = __float2bfloat16_rn(r.hi);
-    c = __float2bfloat16_rn((r.hi - __bfloat162float(b)) + r.lo);
+    b = __float2bfloat16_rn(d);
+    c = __float2bfloat16_rn((d - __bfloat162float(b)) + x.lo);
 }
 
 __device__ __forceinline__ void store_fixed8v(uint8_t *dst, long long plane, const df *x, const float *scale,
@@ -718,21 +720,23 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
     }
 }
 
-// FP32 value -> signed fixed point with unit 2^-40 (round to nearest), from
-// the IEEE bit pattern with integer operations only.  |f| must stay below
-// 2^22; larger or non-finite values set *bad.
+// FP32 value -> signed fixed point with unit 2^-40.  With t = v 2^8,
+// h = rint(t) and f = t - h (exact, |f| <= 1/2), the value is
+// h 2^32 + trunc(f 2^32): two 32-bit conversions instead of 64-bit shifts.
+// The bits below 2^-40 are dropped toward zero (f = +1/2 exactly saturates
+// the low word, an error of one unit).  |v| must stay below 2^22; larger or
+// non-finite values set *bad.
 constexpr int kFixBits = 40;
 
-__device__ __forceinline__ long long f32_to_fix(float f, bool &bad)
+__device__ __forceinline__ long long f32_to_fix(float v, bool &bad)
 {
-    const unsigned u = __float_as_uint(f);
-    const int e = (int)((u >> 23) & 0xFFu);
-    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
-    const int sh = e - 150 + kFixBits;                      // f = m 2^(e-150)
-    bad |= sh > 38;
-    long long r = sh >= 0 ? (m << min(sh, 38)) : (m >> min(-sh, 63));   // truncation below 2^-40
-    r = e == 0 ? 0 : r;                                     // zero or below 1.2e-38
-    return (int)u < 0 ? -r : r;
+    const float t = v * 256.f;
+    bad |= !(fabsf(t) < 1073741824.f);                 // 2^30; also catches NaN
+    const float h = rintf(t);
+    const float f = t - h;
+    const int hi = __float2int_rz(h);
+    const int lo = __float2int_rz(f * 4294967296.f);
+    return (long long)hi * 4294967296ll + (long long)lo;
 }
 
 // h[k] = (accumulate ? h[k] : 0) + acc[k] 2^-40
@@ -769,6 +773,21 @@ struct ColRef {                                  // column i of an H tile (a row
     long long rpl;                               // first stored value of row i minus i's index in its atom
     int atom;                                    // global atom
     int loc;                                     // atom index inside its system
+    int slot;                                    // i's atom among the tile's column atoms (0 = first)
+    int pad;
+};
+
+// Pair offsets of an H tile: for each of the (at most kColAtoms) atoms of
+// the tile's columns and each row j, the start of that atom's run in row i
+// relative to (rp_i - li), i.e. 0 for j's own atom, pairpos otherwise (-1:
+// not stored).  Filled once per tile so that the scatter loop has no
+// dependent global loads.
+constexpr int kColAtoms = 32;
+struct HPairTab {
+    int pp[kColAtoms][128];
+    int2 atom[2][kColAtoms];                     // (global atom, index in system) per slot
+    int nslot[2];
+    int pad[2];
 };
 
 struct TcRing {
@@ -840,6 +859,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
     TcRing *S = reinterpret_cast<TcRing *>(sm + kStages * kStageBytes);
+    HPairTab *PT = reinterpret_cast<HPairTab *>(
+        (reinterpret_cast<uintptr_t>(S + 1) + 15) & ~(uintptr_t)15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) ring_init(S);
     if (warp == kWarpMma) {
@@ -932,19 +953,36 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
             const DevAct *act = P.act + B.act0;
             const int buf = lt & 1, use = lt >> 1;
             const int i0 = it.ti * 128, j0 = it.tj * 128;
+            const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
+            const int nat = P.sys_nat[B.sys];
             if (threadIdx.x < 128) {
                 const int i = i0 + threadIdx.x;
-                if (i < B.nfn) {
-                    const FnRef c = fn_ref(P, act, find_act(act, B.n_act, i), i);
-                    S->ref[buf][threadIdx.x] = ColRef{c.rp - c.li, c.atom, c.loc};
+                const int ilast = min(i0 + 127, B.nfn - 1);
+                if (i <= ilast) {
+                    const int e_first = find_act(act, B.n_act, i0);
+                    const int e = find_act(act, B.n_act, i);
+                    const FnRef c = fn_ref(P, act, e, i);
+                    const int slot = e - e_first;
+                    S->ref[buf][threadIdx.x] = ColRef{c.rp - c.li, c.atom, c.loc, slot, 0};
+                    if (slot < kColAtoms && (i == i0 || act[e].fn_loc == i))
+                        PT->atom[buf][slot] = make_int2(c.atom, c.loc);
+                    if (i == ilast) PT->nslot[buf] = slot + 1;
                 }
             }
             const int r = quad * 32 + lane;
             const int j = j0 + r;                  // this lane's function (block J)
             FnRef jref{};
             if (j < B.nfn) jref = fn_ref(P, act, find_act(act, B.n_act, j), j);
-            const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
-            const int nat = P.sys_nat[B.sys];
+            epi_sync();
+            // pair offsets of this tile (the previous tile's scatter is over)
+            const int nslot = PT->nslot[buf];
+            const bool tab = nslot <= kColAtoms;
+            if (tab && j < B.nfn) {
+                for (int sl = half; sl < nslot; sl += 2) {
+                    const int2 a = PT->atom[buf][sl];
+                    PT->pp[sl][r] = a.x == jref.atom ? 0 : __ldg(pp_sys + (long long)a.y * nat + jref.loc);
+                }
+            }
             epi_sync();
             const bool ok = mbar_wait_a(&S->tfull[buf], (uint32_t)(use & 1), P.status, &S->abort);
             tc_fence_after();
@@ -968,7 +1006,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     const int i = i0 + il;
                     if (i >= B.nfn || i > j) continue;
                     const ColRef ci = S->ref[buf][il];
-                    if (ci.atom != cur_atom) {
+                    if (tab) {
+                        ppv = PT->pp[ci.slot][r];
+                        stored = ppv >= 0;
+                    } else if (ci.atom != cur_atom) {       // more column atoms than table slots
                         cur_atom = ci.atom;
                         if (ci.atom == jref.atom) {
                             ppv = 0;
@@ -1374,12 +1415,14 @@ size_t smem_tc(int n_split)
 
 size_t smem_phi() { return 128 * kPhiValStride * sizeof(float2); }
 
+size_t smem_tc_h() { return smem_tc(3) + sizeof(HPairTab) + 16; }
+
 bool attrs_set = false;
 
 cudaError_t set_attrs()
 {
     if (attrs_set) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
+    cudaError_t e = cudaFuncSetAttribute(k_tc_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc_h());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tc_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
     if (e != cudaSuccess) return e;
@@ -1640,7 +1683,7 @@ cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, cons
 {
     if (w.nh <= 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(w.nh, t.num_sms);
-    k_tc_h<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.h0, (int)w.nh,
+    k_tc_h<<<grid, kThreadsTc, smem_tc_h(), s>>>(P, t.d_batches, t.d_items + w.h0, (int)w.nh,
                                                 (const uint8_t *)ws + t.img_base, (unsigned long long *)ws, n_split);
     return cudaGetLastError();
 }
