@@ -967,6 +967,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     if (slot < kColAtoms && (i == i0 || act[e].fn_loc == i))
                         PT->atom[buf][slot] = make_int2(c.atom, c.loc);
                     if (i == ilast) PT->nslot[buf] = slot + 1;
+                } else {
+                    S->ref[buf][threadIdx.x] = ColRef{0, -1, 0, 0, 0};   // past the batch: a valid slot, never stored
                 }
             }
             const int r = quad * 32 + lane;
@@ -997,7 +999,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                 if (!ok || j >= B.nfn) continue;
                 // stored value of (i, j), i <= j: row i, (rp_i - li) + [pair offset of
                 // atom(j) in row i, 0 for the same atom] + lj
-                int cur_atom = -1;
+                unsigned long long *hj = hfix + jref.li;
+                if (tab) {
+                    // branch-free per column (predicated atomics), so the conversions
+                    // of neighbouring columns overlap
+#pragma unroll
+                    for (int q = 0; q < 32; q++) {
+                        const int il = cc * 32 + q;
+                        const int i = i0 + il;
+                        const long long rpl = S->ref[buf][il].rpl;
+                        const int ppv = PT->pp[S->ref[buf][il].slot][r];
+                        long long fx = f32_to_fix(a0[q], bad);
+                        if (n_split > 1) fx += f32_to_fix(a1[q], bad);
+                        if (i < B.nfn && i <= j && ppv >= 0 && fx != 0)
+                            atomicAdd(hj + rpl + ppv, (unsigned long long)fx);
+                    }
+                    continue;
+                }
+                int cur_atom = -1;                 // more column atoms than table slots
                 int ppv = 0;
                 bool stored = false;
 #pragma unroll
@@ -1006,10 +1025,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     const int i = i0 + il;
                     if (i >= B.nfn || i > j) continue;
                     const ColRef ci = S->ref[buf][il];
-                    if (tab) {
-                        ppv = PT->pp[ci.slot][r];
-                        stored = ppv >= 0;
-                    } else if (ci.atom != cur_atom) {       // more column atoms than table slots
+                    if (ci.atom != cur_atom) {
                         cur_atom = ci.atom;
                         if (ci.atom == jref.atom) {
                             ppv = 0;
@@ -1022,7 +1038,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     if (!stored) continue;
                     long long fx = f32_to_fix(a0[q], bad);
                     if (n_split > 1) fx += f32_to_fix(a1[q], bad);
-                    if (fx != 0) atomicAdd(hfix + ci.rpl + ppv + jref.li, (unsigned long long)fx);
+                    if (fx != 0) atomicAdd(hj + ci.rpl + ppv, (unsigned long long)fx);
                 }
             }
             tc_fence_before();
