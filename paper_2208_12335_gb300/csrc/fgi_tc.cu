@@ -480,8 +480,9 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 
 constexpr int kPhiThreads = 256;
 
-__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                uint8_t *ws, const double *v, int n_split, int fixed)
+__global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                uint8_t *ws, const double *v, int n_split, int fixed,
+                                                int *bsign)
 {
     extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
     __shared__ float2 wv[32];
@@ -501,16 +502,32 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
     const int ne = e1 - e0 + 1;
     uint8_t *phi_img = ws + T.img_phi;
     uint8_t *a_img = ws + T.img_aux;
+    // sign of w v over the batch: one sign s (or zero) everywhere lets H use a
+    // single image psi = phi sqrt|w v| for both operands, H = s psi^T psi;
+    // mixed signs keep the phi and w v phi images
+    bool pos = false, neg = false;
+    for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
+        const double wv = P.pw[B.pt0 + p] * v[B.pt0 + p];
+        pos |= wv > 0.0;
+        neg |= wv < 0.0;
+    }
+    pos = __syncthreads_or(pos) != 0;
+    neg = __syncthreads_or(neg) != 0;
+    const int sgn = (pos && neg) ? 0 : (neg ? -1 : 1);
+    if (I == 0 && threadIdx.x == 0) bsign[it.batch] = sgn;
     if (fixed) {
-        // pass 1: row maxima and sums of |phi| and |w v phi| over the batch's
-        // points (FP32).  One warp per (atom, shell) of the block; lanes stride
-        // over the points and keep per-function partials in registers.
+        // pass 1: row maxima and sums of |phi| and |w v phi| (or of |psi|,
+        // kept in the second set) over the batch's points (FP32).  One warp
+        // per (atom, shell) of the block; lanes stride over the points and
+        // keep per-function partials in registers.
         for (int q = threadIdx.x; q < 256; q += blockDim.x) {
             (&rowmax[0][0])[q] = 0u;          // rows past n_b stay zero
             (&rowsum[0][0])[q] = 0.f;
         }
-        for (int p = threadIdx.x; p < B.np; p += blockDim.x)
-            wvf[p] = fminf(fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p])), 1.0e30f);
+        for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
+            const float a = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p]));
+            wvf[p] = fminf(sgn != 0 ? sqrtf(a) : a, 1.0e30f);
+        }
         __syncthreads();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
         int job = 0;
@@ -595,7 +612,8 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
                 if (!isfinite(vv)) atomicOr(P.status, kStatusNonFinite);
                 s = P.pw[B.pt0 + p] * vv;
             }
-            const df sd = df_from_double(s);
+            df sd = df_from_double(sgn != 0 ? fabs(s) : s);
+            if (sgn != 0) sd = df_sqrt(sd);                 // sqrt|w v| for psi
             wv[threadIdx.x] = make_float2(sd.hi, sd.lo);
         }
         __syncthreads();
@@ -609,21 +627,23 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
                 x[q] = df{t.x, t.y};
             }
             const long long off = unit_offset(I, T.nc_alloc, c, r, g);
-            if (fixed)
-                store_fixed8(phi_img + off, T.plane_phi, x, fsc[0][r][0], fsc[0][r][1]);
-            else
-                store_split8_df(phi_img + off, T.plane_phi, x, n_split);
-            if (v) {
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const float2 s = wv[gg * 8 + q];
-                    x[q] = df_mul(x[q], df{s.x, s.y});
-                }
+            if (sgn == 0) {
                 if (fixed)
-                    store_fixed8(a_img + off, T.plane_phi, x, fsc[1][r][0], fsc[1][r][1]);
+                    store_fixed8(phi_img + off, T.plane_phi, x, fsc[0][r][0], fsc[0][r][1]);
                 else
-                    store_split8_df(a_img + off, T.plane_phi, x, n_split);
+                    store_split8_df(phi_img + off, T.plane_phi, x, n_split);
             }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float2 s = wv[gg * 8 + q];
+                x[q] = df_mul(x[q], df{s.x, s.y});
+            }
+            // w v phi (mixed signs) or psi = phi sqrt|w v| (into the phi image)
+            uint8_t *dst = (sgn == 0 ? a_img : phi_img) + off;
+            if (fixed)
+                store_fixed8(dst, T.plane_phi, x, fsc[1][r][0], fsc[1][r][1]);
+            else
+                store_split8_df(dst, T.plane_phi, x, n_split);
         }
         __syncthreads();
     }
@@ -854,7 +874,7 @@ __device__ __forceinline__ void mma_chunk(uint32_t acc_base, const uint8_t *a_sm
 
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                         int n_items, const uint8_t *ws, unsigned long long *hfix,
-                                                        int n_split)
+                                                        int n_split, const int *bsign)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
@@ -882,8 +902,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                 const TcBatch T = tb[it.batch];
                 // A = phi rows of block J (TMEM lanes), B = w v phi rows of block I
                 // (TMEM columns): the transposed tile, so that the scatter of one
-                // column i by the 32 lanes of a warp hits consecutive values of row i
-                const uint8_t *a_img = ws + T.img_phi, *b_img = ws + T.img_aux;
+                // column i by the 32 lanes of a warp hits consecutive values of row i.
+                // Batches where w v has one sign hold psi = phi sqrt|w v| in the
+                // phi image, which then serves as both operands.
+                const uint8_t *a_img = ws + T.img_phi;
+                const uint8_t *b_img = ws + (bsign[it.batch] != 0 ? T.img_phi : T.img_aux);
                 for (int c = 0; c < T.nc; c++, n++) {
                     const int st = (int)(n % kStages);
                     const long long use = n / kStages;
@@ -975,6 +998,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
             const int j = j0 + r;                  // this lane's function (block J)
             FnRef jref{};
             if (j < B.nfn) jref = fn_ref(P, act, find_act(act, B.n_act, j), j);
+            const bool negate = bsign[it.batch] < 0;            // H = -psi^T psi
             epi_sync();
             // pair offsets of this tile (the previous tile's scatter is over)
             const int nslot = PT->nslot[buf];
@@ -1011,6 +1035,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                         const int ppv = PT->pp[S->ref[buf][il].slot][r];
                         long long fx = f32_to_fix(a0[q], bad);
                         if (n_split > 1) fx += f32_to_fix(a1[q], bad);
+                        if (negate) fx = -fx;
                         if (i < B.nfn && i <= j && ppv >= 0 && fx != 0)
                             atomicAdd(hj + rpl + ppv, (unsigned long long)fx);
                     }
@@ -1038,6 +1063,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_h(DevPlan P, const TcBatch
                     if (!stored) continue;
                     long long fx = f32_to_fix(a0[q], bad);
                     if (n_split > 1) fx += f32_to_fix(a1[q], bad);
+                    if (negate) fx = -fx;
                     if (fx != 0) atomicAdd(hj + ci.rpl + ppv, (unsigned long long)fx);
                 }
             }
@@ -1622,7 +1648,8 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
     t.nnz = in.nnz;
     t.n_fn = in.n_fn;
     t.bound_off = ((size_t)in.nnz * 8 + 255) / 256 * 256;
-    t.img_base = (t.bound_off + 8 * (size_t)in.n_fn + 1023) / 1024 * 1024;
+    t.sign_off = (t.bound_off + 8 * (size_t)in.n_fn + 255) / 256 * 256;
+    t.img_base = (t.sign_off + 4 * (size_t)n_sb + 1023) / 1024 * 1024;
     t.ws_bytes = t.img_base + max_ws + 1024;
     // items must not be empty for the device copy
     if (!in.host_only) {
@@ -1681,7 +1708,8 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     // the H images (v given) of the split mode use the fixed-point leading term
     const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
     k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
-                                                       (uint8_t *)ws + t.img_base, v, n_split, fixed);
+                                                       (uint8_t *)ws + t.img_base, v, n_split, fixed,
+                                                       reinterpret_cast<int *>((uint8_t *)ws + t.sign_off));
     return cudaGetLastError();
 }
 
@@ -1700,7 +1728,8 @@ cudaError_t tc_launch_h(const TcPlan &t, const DevPlan &P, const TcWave &w, cons
     if (w.nh <= 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(w.nh, t.num_sms);
     k_tc_h<<<grid, kThreadsTc, smem_tc_h(), s>>>(P, t.d_batches, t.d_items + w.h0, (int)w.nh,
-                                                (const uint8_t *)ws + t.img_base, (unsigned long long *)ws, n_split);
+                                                (const uint8_t *)ws + t.img_base, (unsigned long long *)ws, n_split,
+                                                reinterpret_cast<const int *>((const uint8_t *)ws + t.sign_off));
     return cudaGetLastError();
 }
 

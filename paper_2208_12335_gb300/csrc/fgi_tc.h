@@ -62,6 +62,7 @@ struct TcPlan {
     size_t wave_cap = 0;
     size_t img_base = 0;                 // workspace offset of the wave images (scratch below)
     size_t bound_off = 0;                // workspace offset of the per-function bounds of D
+    size_t sign_off = 0;                 // workspace offset of the per-batch sign of w v (H images)
     long long nnz = 0, n_fn = 0;
     int num_sms = 1;                     // persistent grids: one CTA per SM
     std::vector<DevBatch> sb;            // super-batches (points, union of active atoms)

@@ -229,3 +229,28 @@ def test_split_h_is_bitwise_reproducible(fgi, si64_sub):
     h3 = ctx.integrate_h(v, h2.clone(), accumulate=True)
     ctx.sync()
     assert torch.allclose(h3, 2 * h1, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_sign_changing_potential(fgi, si64_sub, precision, tol):
+    """A potential that changes sign inside some batches and keeps one sign in
+    others: batches of one sign use the single psi = phi sqrt|w v| image,
+    mixed batches the phi and w v phi images; both must match the oracle."""
+    prob, B, sub, _ = si64_sub
+    v = prob.v + 0.25 * np.abs(prob.v).mean()
+    per_batch = [np.sign(v[prob.batch_off[b]:prob.batch_off[b + 1]]) for b in range(prob.n_batch)]
+    assert any(np.all(s > 0) for s in per_batch) and any(np.all(s < 0) for s in per_batch)
+    assert any((s > 0).any() and (s < 0).any() for s in per_batch)
+    Hs = O.h_matrix(B, prob.pts, prob.w, v, sub=sub)
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(v)).cpu().numpy()
+    ctx.sync()
+    r, c = rows_cols(ctx)
+    pos = -np.ones(B.n_fn, dtype=np.int64)
+    pos[sub] = np.arange(len(sub))
+    inside = (pos[r] >= 0) & (pos[c] >= 0)
+    ref = np.zeros(len(h))
+    ref[inside] = Hs[pos[r[inside]], pos[c[inside]]]
+    err = np.max(np.abs(h - ref))
+    bound = TOL_FP64 * np.abs(Hs).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(Hs).max())
