@@ -343,9 +343,10 @@ __device__ __forceinline__ void fixed_scale_adaptive(float mx, float sum, int de
 }
 
 
-// FP32 phi of one atom's functions at one point (first pass of the H images:
-// only the row maxima are taken from it)
-__device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const float4 *coef_dd, float d)
+// FP32 u(d)/d^(l+1) for the first passes, which only take maxima and sums
+// of |phi| from it (a relative error of a few ulp is far inside the 2^-12
+// margin of the fixed-point grids); inv_d = 1/d, computed once per point.
+__device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const float4 *coef_dd, float d, float inv_d)
 {
     if (d >= R.rcut_f) return 0.f;
     if (d < 1e-12f) return R.l == 0 ? __ldg(coef_dd + 2 * R.coef_off).y * R.inv_h_hi : 0.f;
@@ -354,10 +355,10 @@ __device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const flo
     if (k > R.nk - 2) k = R.nk - 2;
     const float t = s - (float)k;
     const float4 c = __ldg(coef_dd + 2 * (R.coef_off + k));
-    float u = c.x + t * (c.y + t * (c.z + t * c.w));
-    float r = u / d;
-    for (int q = 0; q < R.l; q++) r /= d;
-    return r;
+    const float u = c.x + t * (c.y + t * (c.z + t * c.w));
+    const float i2 = inv_d * inv_d;
+    const float ip = R.l == 0 ? inv_d : (R.l == 1 ? i2 : (R.l == 2 ? i2 * inv_d : i2 * i2));
+    return u * ip;
 }
 
 constexpr int kPhiValStride = 33;   // float2 per row of phi_smem (32 points + padding)
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
                     const float *pp = P.pts_dd + 6 * (B.pt0 + p);
                     const float x = (pp[0] + pp[1]) - ax, y = (pp[2] + pp[3]) - ay, z = (pp[4] + pp[5]) - az;
                     const float d = sqrtf(x * x + y * y + z * z);
-                    const float rad = radial_over_d_f32(R, P.coef_dd, d);
+                    const float rad = radial_over_d_f32(R, P.coef_dd, d, __frcp_rn(d));
                     if (rad == 0.f) continue;
                     float Q[7];
                     int ci[7];
@@ -684,10 +685,11 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
             const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
             const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
             const float d = sqrtf(x * x + y * y + z * z);
+            const float inv_d = __frcp_rn(d);
             float mx = 0.f, sm = 0.f;
             for (int sh = 0; sh < S.n_shell; sh++) {
                 const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
-                const float rad = radial_over_d_f32(R, P.coef_dd, d);
+                const float rad = radial_over_d_f32(R, P.coef_dd, d, inv_d);
                 float Q[7];
                 int ci[7];
                 ylm_poly_f32(R.l, x, y, z, Q, ci);
