@@ -420,16 +420,37 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     std::vector<float> pts_dd = to_dd(c->pts), atom_dd = to_dd(c->atom_xyz);
     std::vector<DevSpecies> dsp;
     std::vector<int> shell_rad;
+    // species whose shells share one knot grid also get their coefficients
+    // interleaved by interval, so that one point's shells read neighbouring
+    // cache lines
+    std::vector<float> scoef;
     for (const SpeciesH &s : c->species) {
-        DevSpecies d;
+        DevSpecies d{};
         d.shell0 = (int)shell_rad.size();
         d.n_shell = (int)s.shells.size();
         d.n_fn = s.n_fn;
-        d.pad = 0;
         d.rcut = s.rcut;
+        bool shared = !s.shells.empty();
+        for (int sh : s.shells)
+            shared = shared && c->radials[sh].h == c->radials[s.shells[0]].h &&
+                     c->radials[sh].nk == c->radials[s.shells[0]].nk;
+        d.shared_grid = shared ? 1 : 0;
+        if (shared) {
+            const RadialH &r0 = c->radials[s.shells[0]];
+            d.nk = r0.nk;
+            d.inv_h_hi = (float)(1.0 / r0.h);
+            d.inv_h_lo = (float)(1.0 / r0.h - (double)d.inv_h_hi);
+            d.scoef_off = (long long)(scoef.size() / 4);
+            for (int k = 0; k < r0.nk - 1; k++)
+                for (int sh : s.shells) {
+                    const size_t src = 8 * ((size_t)drad[sh].coef_off + k);
+                    scoef.insert(scoef.end(), coef_dd.begin() + src, coef_dd.begin() + src + 8);
+                }
+        }
         shell_rad.insert(shell_rad.end(), s.shells.begin(), s.shells.end());
         dsp.push_back(d);
     }
+    if (scoef.empty()) scoef.assign(8, 0.f);
     std::vector<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
     for (int64_t p = 0; p < c->n_pts; p++) {
         px[p] = c->pts[3 * p];
@@ -478,6 +499,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_shr = add(shell_rad.data(), shell_rad.size() * 4),
            i_rad = add(drad.data(), drad.size() * sizeof(DevRadial)),
            i_coef = add(coef.data(), coef.size() * 8), i_coefdd = add(coef_dd.data(), coef_dd.size() * 4),
+           i_scoef = add(scoef.data(), scoef.size() * 4),
            i_ptsdd = add(pts_dd.data(), pts_dd.size() * 4), i_atdd = add(atom_dd.data(), atom_dd.size() * 4),
            i_snat = add(sys_nat.data(), sys_nat.size() * 4),
            i_spo = add(c->sys_pair_off.data(), c->sys_pair_off.size() * 8),
@@ -514,6 +536,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     P.radials = (const DevRadial *)at(i_rad);
     P.coef = (const double *)at(i_coef);
     P.coef_dd = (const float4 *)at(i_coefdd);
+    P.scoef = (const float4 *)at(i_scoef);
     P.pts_dd = (const float *)at(i_ptsdd);
     P.atom_dd = (const float *)at(i_atdd);
     P.sys_nat = (const int *)at(i_snat);

@@ -29,8 +29,12 @@ struct DevSpecies {
     int shell0;           // first entry in shell_rad[]
     int n_shell;
     int n_fn;
-    int pad;
+    int shared_grid;      // 1: every shell's spline uses the same knots (scoef holds them interleaved)
     double rcut;          // largest cutoff of the species' radials
+    long long scoef_off;  // shared grid: first float4 of the species in scoef
+    int nk;               // shared grid: knots
+    float inv_h_hi, inv_h_lo;   // shared grid: 1/h as a double-float
+    int pad;
 };
 
 struct DevBatch {
@@ -68,6 +72,7 @@ struct DevPlan {
     const DevRadial *radials;
     const double *coef;           // [sum intervals][4] FP64
     const float4 *coef_dd;        // [sum intervals][2]: the four coefficients as double-floats (hi, lo)
+    const float4 *scoef;          // species on one knot grid: [interval][shell][2], the same double-floats
     const float *pts_dd;          // [n_pts][6]: x, y, z as double-floats (xh, xl, yh, yl, zh, zl)
     const float *atom_dd;         // [n_atoms][6]: the same for atom positions
     // systems

@@ -346,15 +346,17 @@ __device__ __forceinline__ void fixed_scale_adaptive(float mx, float sum, int de
 // FP32 u(d)/d^(l+1) for the first passes, which only take maxima and sums
 // of |phi| from it (a relative error of a few ulp is far inside the 2^-12
 // margin of the fixed-point grids); inv_d = 1/d, computed once per point.
-__device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const float4 *coef_dd, float d, float inv_d)
+// tab: the radial's interval-0 entry (hi coefficients), entries `step` float4 apart.
+__device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const float4 *tab, int step, float d,
+                                                   float inv_d)
 {
     if (d >= R.rcut_f) return 0.f;
-    if (d < 1e-12f) return R.l == 0 ? __ldg(coef_dd + 2 * R.coef_off).y * R.inv_h_hi : 0.f;
+    if (d < 1e-12f) return R.l == 0 ? __ldg(tab).y * R.inv_h_hi : 0.f;
     const float s = d * R.inv_h_hi;
     int k = (int)s;
     if (k > R.nk - 2) k = R.nk - 2;
     const float t = s - (float)k;
-    const float4 c = __ldg(coef_dd + 2 * (R.coef_off + k));
+    const float4 c = __ldg(tab + (long long)k * step);
     const float u = c.x + t * (c.y + t * (c.z + t * c.w));
     const float i2 = inv_d * inv_d;
     const float ip = R.l == 0 ? inv_d : (R.l == 1 ? i2 : (R.l == 2 ? i2 * inv_d : i2 * i2));
@@ -362,6 +364,19 @@ __device__ __forceinline__ float radial_over_d_f32(const DevRadial &R, const flo
 }
 
 constexpr int kPhiValStride = 33;   // float2 per row of phi_smem (32 points + padding)
+
+// Interval-0 entry of shell sh's spline and the distance between interval
+// entries: the species' interleaved table when its shells share one grid.
+__device__ __forceinline__ const float4 *spline_tab(const DevPlan &P, const DevSpecies &S, const DevRadial &R, int sh,
+                                                    int &step)
+{
+    if (S.shared_grid) {
+        step = 2 * S.n_shell;
+        return P.scoef + S.scoef_off + 2 * sh;
+    }
+    step = 2;
+    return P.coef_dd + 2 * R.coef_off;
+}
 
 // The 2l+1 values N_lm u(d)/d^(l+1) Q_lm(x, y, z) of one shell (functions
 // f0 .. f0+2l of the atom; only those in [f_lo, f_hi) are written): the
@@ -422,6 +437,14 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
         // knot interval and offset, shared by consecutive shells on the same knot grid
         float grid_hi = -1.f, grid_lo = 0.f, t = 0.f;
         int grid_nk = -1, kk = 0;
+        const float4 *sc = nullptr;            // species on one grid: this point's interval row
+        if (S.shared_grid && !origin) {
+            const df sd = df_mul(d, df{S.inv_h_hi, S.inv_h_lo});
+            kk = (int)floorf(sd.hi);
+            kk = max(0, min(kk, S.nk - 2));
+            t = (sd.hi - (float)kk) + sd.lo;
+            sc = P.scoef + S.scoef_off + 2 * ((long long)kk * S.n_shell);
+        }
         for (int sh = 0; sh < S.n_shell; sh++) {
             const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
             const int nm = 2 * R.l + 1;
@@ -439,17 +462,23 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                 } else {
                     // t = frac(d/h) from the double-float d; u = c0 + t (c1 + t (c2 + t c3))
                     // with c0 in double-float and the (smaller) polynomial tail in FP32
-                    if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
-                        grid_hi = R.inv_h_hi;
-                        grid_lo = R.inv_h_lo;
-                        grid_nk = R.nk;
-                        const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
-                        kk = (int)floorf(s.hi);
-                        kk = max(0, min(kk, R.nk - 2));
-                        t = (s.hi - (float)kk) + s.lo;
+                    const float4 *ce;
+                    if (sc) {
+                        ce = sc + 2 * sh;
+                    } else {
+                        if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
+                            grid_hi = R.inv_h_hi;
+                            grid_lo = R.inv_h_lo;
+                            grid_nk = R.nk;
+                            const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
+                            kk = (int)floorf(s.hi);
+                            kk = max(0, min(kk, R.nk - 2));
+                            t = (s.hi - (float)kk) + s.lo;
+                        }
+                        ce = P.coef_dd + 2 * (R.coef_off + kk);
                     }
-                    const float4 ch = __ldg(P.coef_dd + 2 * (R.coef_off + kk));
-                    const float c0lo = __ldg(reinterpret_cast<const float *>(P.coef_dd + 2 * (R.coef_off + kk) + 1));
+                    const float4 ch = __ldg(ce);
+                    const float c0lo = __ldg(reinterpret_cast<const float *>(ce + 1));
                     const float tail = t * (ch.y + t * (ch.z + t * ch.w));
                     df uu = df_two_sum(ch.x, tail);
                     uu = df_fast_two_sum(uu.hi, uu.lo + c0lo);
@@ -546,6 +575,8 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
                 f += nm;
                 if (f <= f_lo || f1 >= f_hi) continue;
                 if ((job++ % nwarp) != warp) continue;
+                int tstep;
+                const float4 *tab = spline_tab(P, S, R, sh, tstep);
                 float mx[7], sm[7], mxw[7], smw[7];
 #pragma unroll
                 for (int m = 0; m < 7; m++) mx[m] = sm[m] = mxw[m] = smw[m] = 0.f;
@@ -553,7 +584,7 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
                     const float *pp = P.pts_dd + 6 * (B.pt0 + p);
                     const float x = (pp[0] + pp[1]) - ax, y = (pp[2] + pp[3]) - ay, z = (pp[4] + pp[5]) - az;
                     const float d = sqrtf(x * x + y * y + z * z);
-                    const float rad = radial_over_d_f32(R, P.coef_dd, d, __frcp_rn(d));
+                    const float rad = radial_over_d_f32(R, tab, tstep, d, __frcp_rn(d));
                     if (rad == 0.f) continue;
                     float Q[7];
                     int ci[7];
@@ -689,7 +720,9 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
             float mx = 0.f, sm = 0.f;
             for (int sh = 0; sh < S.n_shell; sh++) {
                 const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
-                const float rad = radial_over_d_f32(R, P.coef_dd, d, inv_d);
+                int tstep;
+                const float4 *tab = spline_tab(P, S, R, sh, tstep);
+                const float rad = radial_over_d_f32(R, tab, tstep, d, inv_d);
                 float Q[7];
                 int ci[7];
                 ylm_poly_f32(R.l, x, y, z, Q, ci);
