@@ -117,8 +117,14 @@ int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w
 
 /* Build the plan (host, once per geometry and grid): the functions active
    on each batch, the sparsity pattern of H, the tile work lists, and the
-   device copies of the inputs.  tune_cache_path: NULL for default tiles, or
-   a file of tuned settings written by the autotuner. */
+   device copies of the inputs.  tune_cache_path: NULL for the defaults, or a
+   text file of "key value" lines written by the autotuner
+   (paper_2208_12335_gb300/tune.py): density_sb_points (points per density
+   super-batch, 0..1024; 0 keeps the given batches), density_sb_growth (limit
+   on a super-batch's active functions relative to its largest member,
+   1..16), wave_mb (operand-image workspace per wave, MiB).  A missing file
+   means the defaults; a malformed or out-of-range value is FGI_ERR_ARG.
+   The paper has no counterpart for the settings (it prints no kernel). */
 int fgi_plan(fgi_ctx *ctx, fgi_precision precision, const char *tune_cache_path);
 
 /* Change the precision of later compute calls without re-planning. */

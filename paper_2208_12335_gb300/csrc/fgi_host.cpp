@@ -170,16 +170,77 @@ void wave_work(fgi_ctx *c);
 // Two tensor-core plans: H keeps the batches as given (its split accuracy
 // depends on the points per contraction), the density merges neighbouring
 // batches into super-batches of up to 1024 points (its accuracy does not).
+// Tuned settings: a text file of "key value" lines (the autotuner writes it):
+//   density_sb_points  super-batch point limit of the density path (0: none, <= 1024)
+//   density_sb_growth  limit on a super-batch's functions / its largest member's
+//   wave_mb            operand-image workspace per wave, MiB
+// Unknown keys are ignored; a malformed value is an argument error.
+struct TuneSettings {
+    int sb_points = 1024;
+    double sb_growth = 1.35;
+    long long wave_mb = 0;      // 0: the library default
+};
+
+int read_tune_file(const char *path, TuneSettings &t, std::string *err)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return FGI_OK;      // no file yet: the defaults
+    char key[64];
+    double val;
+    int rc = FGI_OK;
+    while (true) {
+        const int n = fscanf(f, "%63s %lf", key, &val);
+        if (n == EOF) break;
+        if (n != 2) {
+            *err = std::string("tune file ") + path + ": expected 'key value' lines";
+            rc = FGI_ERR_ARG;
+            break;
+        }
+        const std::string k(key);
+        if (k == "density_sb_points") {
+            if (!(val >= 0 && val <= kMaxBatchPoints)) {
+                *err = "tune file: density_sb_points out of range";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.sb_points = (int)val;
+        } else if (k == "density_sb_growth") {
+            if (!(val >= 1.0 && val <= 16.0)) {
+                *err = "tune file: density_sb_growth out of range";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.sb_growth = val;
+        } else if (k == "wave_mb") {
+            if (!(val >= 1.0)) {
+                *err = "tune file: wave_mb out of range";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.wave_mb = (long long)val;
+        }
+    }
+    fclose(f);
+    return rc;
+}
+
 int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
 {
+    TuneSettings ts;
+    if (tin.tune_path) {
+        const int rc = read_tune_file(tin.tune_path, ts, err);
+        if (rc != FGI_OK) return rc;
+    }
+    // environment overrides for experiments
+    if (const char *e = getenv("FGI_SB_POINTS")) ts.sb_points = atoi(e);
+    if (const char *e = getenv("FGI_SB_GROWTH")) ts.sb_growth = atof(e);
+    tin.wave_mb = ts.wave_mb;
     tin.sb_points = 0;
     tin.sb_growth = 1.0;
     int rc = tc_build(c->tc, tin, err);
     if (rc != FGI_OK) return rc;
-    tin.sb_points = 1024;
-    tin.sb_growth = 1.35;
-    if (const char *e = getenv("FGI_SB_POINTS")) tin.sb_points = atoi(e);
-    if (const char *e = getenv("FGI_SB_GROWTH")) tin.sb_growth = atof(e);
+    tin.sb_points = ts.sb_points;
+    tin.sb_growth = ts.sb_growth;
     return tc_build(c->tcd, tin, err);
 }
 

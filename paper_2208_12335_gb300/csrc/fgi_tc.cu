@@ -1579,6 +1579,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
     t.items.clear();
     t.waves.clear();
     size_t cap = (size_t)24 << 30;   // workloads up to ~24 GB of operand images run as one wave
+    if (in.wave_mb > 0) cap = (size_t)in.wave_mb << 20;
     if (const char *e = getenv("FGI_TC_WAVE_MB")) cap = (size_t)std::max(1L, atol(e)) << 20;
     t.wave_cap = cap;
     // per-batch image geometry and footprint (3 planes always reserved)

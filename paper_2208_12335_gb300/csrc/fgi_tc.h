@@ -54,6 +54,7 @@ struct TcPlanInput {
     double sb_growth = 1.0;              // limit on the union's functions / largest member's
     long long n_fn = 0;                  // functions (all systems)
     bool host_only = false;              // build host tables only (no device copies)
+    long long wave_mb = 0;               // operand images per wave, MiB (0: default)
 };
 
 struct TcPlan {

@@ -195,3 +195,22 @@ def test_batch_work_counts_points_and_covers_the_nonzero_functions(fgi):
     with pytest.raises(fgi.FGIError) as e:
         ctx._check(ctx._lib.fgi_get_batch_work(ctx._h, sub.n_batch + 1, None, None))
     assert e.value.code == -1
+
+
+def test_tune_file_is_read_and_checked(fgi, water, tmp_path):
+    from paper_2208_12335_gb300 import tune as T
+    good = tmp_path / "good.txt"
+    T.write_settings(str(good), {"density_sb_points": 512, "density_sb_growth": 1.2, "wave_mb": 256})
+    assert T.read_settings(str(good)) == {"density_sb_points": 512.0, "density_sb_growth": 1.2, "wave_mb": 256.0}
+    ctx = host_ctx(fgi, water)
+    ctx.plan("split_bf16", str(good))
+    ctx.plan("split_bf16", str(tmp_path / "missing.txt"))          # no file: the defaults
+    bad = tmp_path / "bad.txt"
+    bad.write_text("density_sb_points 4096\n")
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("split_bf16", str(bad))
+    assert e.value.code == -1
+    bad.write_text("density_sb_growth\n")
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("split_bf16", str(bad))
+    assert e.value.code == -1

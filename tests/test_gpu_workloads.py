@@ -146,3 +146,19 @@ def test_split_step_replays_as_a_cuda_graph(fgi):
     torch.cuda.synchronize()
     assert torch.equal(h, h_eager)                      # fixed-point H: bitwise
     assert torch.allclose(n, n_eager, rtol=0, atol=1e-14)
+
+
+def test_autotuner_writes_settings_that_plan_and_keep_parity(fgi, tmp_path):
+    from paper_2208_12335_gb300 import tune as T
+    prob = W.tiny_water()
+    path = str(tmp_path / "tuned.txt")
+    cands = [{"density_sb_points": 0}, {"density_sb_points": 1024, "density_sb_growth": 1.35}]
+    res = T.tune(prob, path, candidates=cands, steps=2)
+    assert res["best"] in cands and len(res["ms"]) == 2 and all(ms > 0 for ms in res["ms"].values())
+    B = O.system_basis(prob)
+    H = O.h_matrix(B, prob.pts, prob.w, prob.v)
+    ctx = fgi.Context(0).load(prob, "split_bf16", tune_path=path)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()
+    r, c = rows_cols(ctx)
+    assert np.max(np.abs(h - H[r, c])) <= 1e-7
