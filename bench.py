@@ -186,7 +186,8 @@ def oracle_sample(prob, D, n_batches, seed=7):
     sample of batches; returns (points, seconds, threads)."""
     import oracle as O
     rng = np.random.default_rng(seed)
-    ids = np.sort(rng.choice(prob.n_batch, size=min(n_batches, prob.n_batch), replace=False))
+    cand = np.nonzero(prob.batch_sys == 0)[0]          # system 0 (D and the basis are its)
+    ids = np.sort(rng.choice(cand, size=min(n_batches, len(cand)), replace=False))
     sub = prob.subgrid(ids)
     B = O.system_basis(sub)
     act = O.active_functions(B, sub.pts)
@@ -272,7 +273,18 @@ def main():
     ctx = Context(local).load(prob, args.precision)
     plan_s = time.perf_counter() - t0
     n_fn, nnz, n_pts, n_at = ctx.sizes()
-    if D is not None:
+    if prob.n_sys > 1:
+        # one occupied-orbital density matrix per system; system 0 is checked
+        rng = W.rng_for(1, W.PURPOSE_D)
+        dvals = np.zeros(nnz)
+        for s_ in range(prob.n_sys):
+            _, nf, val0, nn = ctx.system(s_)
+            Ds, _ = W.density_matrix_occ(nf, max(1, int(round(0.28 * nf))), rng)
+            vals, r_, c_ = stored_values(ctx, Ds, s_)
+            dvals[val0:val0 + nn] = vals
+            if s_ == 0:
+                D, rows, cols = Ds, r_, c_
+    elif D is not None:
         dvals, rows, cols = stored_values(ctx, D)
     else:
         rng = W.rng_for(2, W.PURPOSE_D)
@@ -456,11 +468,12 @@ def check_against_oracle(prob, ctx, h, n, D, rows, cols, n_pairs=48, n_points=25
     """Sampled outputs against the FP64 oracle computed one by one."""
     import oracle as O
     rng = np.random.default_rng(2024)
-    B = O.system_basis(prob)
+    B = O.system_basis(prob, 0)                  # system 0 (values first in H, CSR order)
+    p0 = prob.system_points(0)
     hv = h.cpu().numpy()
-    k = rng.choice(len(hv), size=n_pairs, replace=False)
-    ref = O.h_pairs(B, prob.pts, prob.w, prob.v, rows[k], cols[k])
-    pts = rng.choice(prob.n_pts, size=n_points, replace=False)
+    k = rng.choice(len(rows), size=min(n_pairs, len(rows)), replace=False)
+    ref = O.h_pairs(B, prob.pts[p0], prob.w[p0], prob.v[p0], rows[k], cols[k])
+    pts = p0[rng.choice(len(p0), size=min(n_points, len(p0)), replace=False)]
     nref = O.density(B, prob.pts[pts], D)
     nv = n.cpu().numpy()[pts]
     return {"max_abs_dH_sampled": float(np.max(np.abs(hv[k] - ref))),
