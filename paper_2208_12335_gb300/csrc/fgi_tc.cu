@@ -558,6 +558,22 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
             const float a = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p]));
             wvf[p] = fminf(sgn != 0 ? sqrtf(a) : a, 1.0e30f);
         }
+        // FP32 offsets and distances of the block's atoms to the batch's points,
+        // once, in the (not yet used) value buffer when they fit: every shell
+        // job of an atom reads them instead of recomputing them
+        float4 *geo = reinterpret_cast<float4 *>(phi_smem);
+        const bool geo_cached = ne * B.np <= 128 * kPhiValStride / 2;    // float4 slots of the buffer
+        if (geo_cached) {
+            for (int q = threadIdx.x; q < ne * B.np; q += blockDim.x) {
+                const int eq = q / B.np, p = q - eq * B.np;
+                const float *aa = P.atom_dd + 6 * act[e0 + eq].atom;
+                const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                const float x = (pp[0] + pp[1]) - (aa[0] + aa[1]);
+                const float y = (pp[2] + pp[3]) - (aa[2] + aa[3]);
+                const float z = (pp[4] + pp[5]) - (aa[4] + aa[5]);
+                geo[q] = make_float4(x, y, z, sqrtf(x * x + y * y + z * z));
+            }
+        }
         __syncthreads();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
         int job = 0;
@@ -581,9 +597,20 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
 #pragma unroll
                 for (int m = 0; m < 7; m++) mx[m] = sm[m] = mxw[m] = smw[m] = 0.f;
                 for (int p = lane; p < B.np; p += 32) {
-                    const float *pp = P.pts_dd + 6 * (B.pt0 + p);
-                    const float x = (pp[0] + pp[1]) - ax, y = (pp[2] + pp[3]) - ay, z = (pp[4] + pp[5]) - az;
-                    const float d = sqrtf(x * x + y * y + z * z);
+                    float x, y, z, d;
+                    if (geo_cached) {
+                        const float4 gq = geo[(e - e0) * B.np + p];
+                        x = gq.x;
+                        y = gq.y;
+                        z = gq.z;
+                        d = gq.w;
+                    } else {
+                        const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                        x = (pp[0] + pp[1]) - ax;
+                        y = (pp[2] + pp[3]) - ay;
+                        z = (pp[4] + pp[5]) - az;
+                        d = sqrtf(x * x + y * y + z * z);
+                    }
                     const float rad = radial_over_d_f32(R, tab, tstep, d, __frcp_rn(d));
                     if (rad == 0.f) continue;
                     float Q[7];
