@@ -510,7 +510,7 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 
 constexpr int kPhiThreads = 256;
 
-__global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed,
                                                 int *bsign)
 {
