@@ -174,11 +174,15 @@ void wave_work(fgi_ctx *c);
 //   density_sb_points  super-batch point limit of the density path (0: none, <= 1024)
 //   density_sb_growth  limit on a super-batch's functions / its largest member's
 //   wave_mb            operand-image workspace per wave, MiB
+//   h_sb_points        super-batch point limit of the H path (0: none, <= 1024)
+//   h_sb_growth        the H path's limit on the union's functions / largest member's
 // Unknown keys are ignored; a malformed value is an argument error.
 struct TuneSettings {
     int sb_points = 1024;
     double sb_growth = 1.35;
     long long wave_mb = 0;      // 0: the library default
+    int h_sb_points = 0;
+    double h_sb_growth = 1.25;
 };
 
 int read_tune_file(const char *path, TuneSettings &t, std::string *err)
@@ -211,6 +215,20 @@ int read_tune_file(const char *path, TuneSettings &t, std::string *err)
                 break;
             }
             t.sb_growth = val;
+        } else if (k == "h_sb_points") {
+            if (!(val >= 0 && val <= kMaxBatchPoints)) {
+                *err = "tune file: h_sb_points out of range";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.h_sb_points = (int)val;
+        } else if (k == "h_sb_growth") {
+            if (!(val >= 1.0 && val <= 16.0)) {
+                *err = "tune file: h_sb_growth out of range";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.h_sb_growth = val;
         } else if (k == "wave_mb") {
             if (!(val >= 1.0)) {
                 *err = "tune file: wave_mb out of range";
@@ -234,9 +252,11 @@ int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
     // environment overrides for experiments
     if (const char *e = getenv("FGI_SB_POINTS")) ts.sb_points = atoi(e);
     if (const char *e = getenv("FGI_SB_GROWTH")) ts.sb_growth = atof(e);
+    if (const char *e = getenv("FGI_H_SB_POINTS")) ts.h_sb_points = atoi(e);
+    if (const char *e = getenv("FGI_H_SB_GROWTH")) ts.h_sb_growth = atof(e);
     tin.wave_mb = ts.wave_mb;
-    tin.sb_points = 0;
-    tin.sb_growth = 1.0;
+    tin.sb_points = ts.h_sb_points;
+    tin.sb_growth = ts.h_sb_growth;
     int rc = tc_build(c->tc, tin, err);
     if (rc != FGI_OK) return rc;
     tin.sb_points = ts.sb_points;

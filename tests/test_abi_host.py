@@ -210,6 +210,13 @@ def test_tune_file_is_read_and_checked(fgi, water, tmp_path):
     with pytest.raises(fgi.FGIError) as e:
         ctx.plan("split_bf16", str(bad))
     assert e.value.code == -1
+    bad.write_text("h_sb_points -3\n")
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("split_bf16", str(bad))
+    assert e.value.code == -1
+    ok = tmp_path / "ok.txt"
+    ok.write_text("h_sb_points 256\nh_sb_growth 1.2\n")
+    ctx.plan("split_bf16", str(ok))
     bad.write_text("density_sb_growth\n")
     with pytest.raises(fgi.FGIError) as e:
         ctx.plan("split_bf16", str(bad))
