@@ -287,8 +287,12 @@ def main():
     elif D is not None:
         dvals, rows, cols = stored_values(ctx, D)
     else:
-        rng = W.rng_for(2, W.PURPOSE_D)
-        dvals = rng.standard_normal(nnz) * 0.05
+        # large system: the stored values of the same occupied-orbital D,
+        # computed on the pattern only (no dense n x n matrix); no oracle check
+        rp, cl = ctx.pattern(0)
+        r_ = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        dvals = W.density_values_occ(n_fn, max(1, int(round(0.28 * n_fn))), r_, cl,
+                                     W.rng_for(1, W.PURPOSE_D))
         rows = cols = None
     v = torch.from_numpy(prob.v).to(dev)
     d = torch.from_numpy(dvals).to(dev)

@@ -37,8 +37,9 @@ prints no workload definition, so each choice below is a stated reading):
   |v| below ~Z like a self-consistent potential and lets the sum run over
   atoms within ``v_cut`` Bohr only;
 * D = 2 C_occ C_occ^T with C_occ the first columns of a seeded orthonormal
-  matrix (QR of a Gaussian matrix), or a seeded symmetric random matrix for
-  the large workloads; G = (X + X^T)/2 with X ~ N(0,1);
+  matrix (QR of a Gaussian matrix); for the large workloads only its values
+  on the stored pattern are formed (``density_values_occ``); parity tests
+  also use seeded symmetric random matrices; G = (X + X^T)/2 with X ~ N(0,1);
 * seeds: numpy PCG64 with seed 2208_12335 + 100 * workload_index + purpose
   (0 geometry, 1 basis, 2 D, 3 G, 4 angular rotation, 5 batching).
 """
@@ -720,6 +721,19 @@ def density_matrix_occ(n_fn: int, n_occ: int, rng: np.random.Generator, occ: flo
     q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
     q = q * np.sign(np.diag(r))[None, :]
     return occ * (q @ q.T), q
+
+
+def density_values_occ(n_fn: int, n_occ: int, rows, cols, rng: np.random.Generator, occ: float = 2.0,
+                       chunk: int = 1 << 20):
+    """The stored values D[rows, cols] of D = occ C C^T (C as in
+    density_matrix_occ) without forming the dense n x n matrix."""
+    q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
+    q = q * np.sign(np.diag(r))[None, :]
+    out = np.empty(len(rows))
+    for k0 in range(0, len(rows), chunk):
+        k1 = min(len(rows), k0 + chunk)
+        out[k0:k1] = occ * np.einsum("ij,ij->i", q[rows[k0:k1]], q[cols[k0:k1]])
+    return out
 
 
 def random_symmetric(n: int, rng: np.random.Generator, scale: float = 1.0):
