@@ -292,7 +292,7 @@ def main():
         rp, cl = ctx.pattern(0)
         r_ = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
         dvals = W.density_values_occ(n_fn, max(1, int(round(0.28 * n_fn))), r_, cl,
-                                     W.rng_for(1, W.PURPOSE_D))
+                                     W.rng_for(1, W.PURPOSE_D), accel="cuda:%d" % local)
         rows = cols = None
     v = torch.from_numpy(prob.v).to(dev)
     d = torch.from_numpy(dvals).to(dev)

@@ -724,12 +724,25 @@ def density_matrix_occ(n_fn: int, n_occ: int, rng: np.random.Generator, occ: flo
 
 
 def density_values_occ(n_fn: int, n_occ: int, rows, cols, rng: np.random.Generator, occ: float = 2.0,
-                       chunk: int = 1 << 20):
+                       accel=None, chunk_bytes: int = 1 << 30):
     """The stored values D[rows, cols] of D = occ C C^T (C as in
-    density_matrix_occ) without forming the dense n x n matrix."""
+    density_matrix_occ) without forming the dense n x n matrix; the row
+    dot products run with torch on `accel` when given."""
     q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
     q = q * np.sign(np.diag(r))[None, :]
+    chunk = max(1, chunk_bytes // (8 * max(1, n_occ)))
     out = np.empty(len(rows))
+    if accel is not None:
+        import torch
+        dev = _torch_device(accel)
+        qt = torch.from_numpy(q).to(dev)
+        rt = torch.from_numpy(np.asarray(rows, dtype=np.int64)).to(dev)
+        ct = torch.from_numpy(np.asarray(cols, dtype=np.int64)).to(dev)
+        res = torch.empty(len(rows), dtype=torch.float64, device=dev)
+        for k0 in range(0, len(rows), chunk):
+            k1 = min(len(rows), k0 + chunk)
+            res[k0:k1] = occ * (qt[rt[k0:k1]] * qt[ct[k0:k1]]).sum(dim=1)
+        return res.cpu().numpy()
     for k0 in range(0, len(rows), chunk):
         k1 = min(len(rows), k0 + chunk)
         out[k0:k1] = occ * np.einsum("ij,ij->i", q[rows[k0:k1]], q[cols[k0:k1]])
