@@ -123,8 +123,8 @@ int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w
    super-batch, 0..1024; 0 keeps the given batches), density_sb_growth (limit
    on a super-batch's active functions relative to its largest member,
    1..16), wave_mb (operand-image workspace per wave, MiB), h_sb_points and
-   h_sb_growth (the same two limits for the H path, whose super-batches
-   default to off).  A missing file
+   h_sb_growth (the same two limits for the H path; defaults 400 points and
+   1.25, so only small neighbouring batches merge).  A missing file
    means the defaults; a malformed or out-of-range value is FGI_ERR_ARG.
    The paper has no counterpart for the settings (it prints no kernel). */
 int fgi_plan(fgi_ctx *ctx, fgi_precision precision, const char *tune_cache_path);

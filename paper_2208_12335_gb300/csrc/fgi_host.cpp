@@ -181,7 +181,7 @@ struct TuneSettings {
     int sb_points = 1024;
     double sb_growth = 1.35;
     long long wave_mb = 0;      // 0: the library default
-    int h_sb_points = 0;
+    int h_sb_points = 400;      // merges small neighbouring batches; no deeper K than the largest batches
     double h_sb_growth = 1.25;
 };
 

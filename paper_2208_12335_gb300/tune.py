@@ -23,6 +23,8 @@ from .fgi import Context
 
 DEFAULT_CANDIDATES = [
     {"density_sb_points": 0},
+    {"h_sb_points": 0},
+    {"h_sb_points": 256, "h_sb_growth": 1.25},
     {"density_sb_points": 512, "density_sb_growth": 1.35},
     {"density_sb_points": 768, "density_sb_growth": 1.35},
     {"density_sb_points": 1024, "density_sb_growth": 1.2},
