@@ -349,6 +349,18 @@ def main():
         for kind in ("basis", "h", "density", "other"):
             prof[kind] = ctx.profile_read(kind)
         ctx.profile(False)
+    else:
+        # the graph replays carry no per-kind events: the same steps run
+        # eagerly once more, outside the timed region, for the per-kind
+        # times, launch counts and the roofline line
+        ctx.profile(True)
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            step()
+        ctx.sync()
+        for kind in ("basis", "h", "density", "other"):
+            prof[kind] = ctx.profile_read(kind)
+        ctx.profile(False)
     ctx.sync()
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
