@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
     ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
+    ap.add_argument("--fp64-per-system", action="store_true",
+                    help="many-instance workloads: also time the FP64 path called molecule by molecule")
     ap.add_argument("--batches", type=int, default=0,
                     help="use a seeded subset of this many batches (small cases for profiling)")
     args = ap.parse_args()
@@ -405,6 +407,34 @@ def main():
                 "max_abs_dH_vs_fp64_gpu": float((h - h64).abs().max().item()),
                 "density_rel_l2_vs_fp64_gpu": float(((n - n64).norm() / n64.norm()).item())}
 
+    # many-instance: the FP64 path called molecule by molecule (one context
+    # and plan per molecule, one shared workspace), on the same inputs
+    fp64_loop = None
+    if args.fp64_per_system and prob.n_sys > 1:
+        subs = [prob.system_problem(s_) for s_ in range(prob.n_sys)]
+        ctxs = [Context(local).load(sp, "fp64") for sp in subs]
+        wsb = max(cx.workspace_size() for cx in ctxs)
+        ws64 = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+        ins = []
+        for s_, (sp, cx) in enumerate(zip(subs, ctxs)):
+            _, _, val0, nn = ctx.system(s_)
+            ins.append((torch.from_numpy(sp.v).to(dev), d[val0:val0 + nn].contiguous(),
+                        torch.empty(nn, dtype=torch.float64, device=dev),
+                        torch.empty(sp.n_pts, dtype=torch.float64, device=dev)))
+
+        def loop_step():
+            for cx, (vs, ds, hs, ns) in zip(ctxs, ins):
+                cx.integrate_h(vs, hs, ws=ws64)
+                cx.density(ds, ns, ws=ws64, with_traces=False)
+
+        loop_step()
+        torch.cuda.synchronize()
+        tl = timed(max(1, args.fp64_steps), loop_step)
+        fp64_loop = {"ms_per_step": statistics.mean(tl), "value": n_pts / (statistics.mean(tl) * 1e-3),
+                     "n_contexts": len(ctxs)}
+        for cx in ctxs:
+            cx.close()
+
     out = None
     if rank == 0:
         flops_step = sum(prof[k]["flops"] for k in ("h", "density")) / args.steps if prof else None
@@ -470,6 +500,7 @@ def main():
                        "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
                "gpu_launches": launches * args.steps if launches is not None else None,
                "fp64_path": fp64,
+               "fp64_per_molecule_loop": fp64_loop,
                "errors_vs_oracle": errors,
                "clocks": clk.summary(),
                "profile_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof} if prof else None}

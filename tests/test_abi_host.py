@@ -221,3 +221,19 @@ def test_tune_file_is_read_and_checked(fgi, water, tmp_path):
     with pytest.raises(fgi.FGIError) as e:
         ctx.plan("split_bf16", str(bad))
     assert e.value.code == -1
+
+
+def test_system_problem_extracts_one_molecule(fgi):
+    prob = W.many_molecules(n_mol=3, n_at_range=(3, 5), nrad_range=(16, 18), nang_choices=(50,))
+    for s in range(prob.n_sys):
+        sp = prob.system_problem(s)
+        pts = prob.system_points(s)
+        assert sp.n_sys == 1 and np.array_equal(sp.pts, prob.pts[pts]) and np.array_equal(sp.v, prob.v[pts])
+        a0, a1 = prob.atom_off[s], prob.atom_off[s + 1]
+        assert np.array_equal(sp.atom_xyz, prob.atom_xyz[a0:a1])
+        # the one-system plan has the same pattern as that system's block of the joint plan
+        joint = host_ctx(fgi, prob)
+        alone = host_ctx(fgi, sp)
+        rp_j, col_j = joint.pattern(s)
+        rp_a, col_a = alone.pattern(0)
+        assert np.array_equal(rp_j, rp_a) and np.array_equal(col_j, col_a)

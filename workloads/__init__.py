@@ -214,6 +214,18 @@ class Problem:
             return np.zeros(0, dtype=np.int64)
         return np.arange(self.batch_off[bs[0]], self.batch_off[bs[-1] + 1])
 
+    def system_problem(self, s: int) -> "Problem":
+        """System s alone: its atoms, batches and points (a one-system problem)."""
+        a0, a1 = int(self.atom_off[s]), int(self.atom_off[s + 1])
+        bs = np.nonzero(self.batch_sys == s)[0]
+        p0, p1 = int(self.batch_off[bs[0]]), int(self.batch_off[bs[-1] + 1])
+        off = (self.batch_off[bs[0]:bs[-1] + 2] - p0).astype(np.int64)
+        return Problem("%s-sys%d" % (self.name, s), self.radials, self.species,
+                       np.array([0, a1 - a0], dtype=np.int64), self.atom_species[a0:a1].copy(),
+                       self.atom_xyz[a0:a1].copy(), self.pts[p0:p1].copy(), self.w[p0:p1].copy(), off,
+                       np.zeros(len(bs), dtype=np.int32), self.v[p0:p1].copy(), self.workload_index,
+                       dict(self.meta))
+
     def subgrid(self, batch_ids) -> "Problem":
         """A new problem holding only the listed batches (same geometry)."""
         batch_ids = np.asarray(sorted(batch_ids), dtype=np.int64)
