@@ -442,38 +442,45 @@ def main():
         peaks, peak_src = measured_peaks()
         # dominant kernel class by measured time
         roof = None
+        roof_all = None
         if prof:
+            fp64_peak = fp64_gemm_peak(torch) if args.precision == "fp64" else None
+
+            def roofline(kind):
+                pk = prof[kind]
+                avg_ms = pk["ms"] / max(1, pk["launches"])
+                per_launch_flops = pk["flops"] / max(1, pk["launches"])
+                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
+                if kind == "basis":
+                    # FP32 pipe: SMs x 128 lanes x 2 FLOP (FMA) per clock at the
+                    # sampled maximum SM clock; the algorithmic count is ~30 FLOP
+                    # per (point, function)
+                    mhz = clk.summary().get("sm_max_mhz") or 2070.0
+                    r = {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp32_alu_peak(torch, mhz),
+                         "unit": "TFLOP/s",
+                         "peak_note": "FP32 FMA issue rate: SMs x 128 lanes x 2 FLOP x %.0f MHz" % mhz}
+                elif args.precision == "fp64":
+                    r = {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "peak_note": "measured FP64 GEMM (cuBLAS) on this GPU"}
+                else:
+                    # BF16 products per algorithmic FLOP: split H 8, split density 6
+                    products = ({"h": 8, "density": 6}[kind] if args.precision == "split_bf16" else 1)
+                    r = {"kernel": kind, "bound": "tensor", "achieved": ach,
+                         "peak": peaks["bf16_tflops_sustained"] / products, "unit": "TFLOP/s",
+                         "peak_note": "%s sustained BF16 / %d BF16 products per algorithmic FLOP"
+                                      % (peak_src, products)}
+                r["frac"] = r["achieved"] / r["peak"]
+                # the committed DRAM figures were taken on the split-BF16 kernels
+                r["traffic"] = traffic_for(kind) if args.precision == "split_bf16" else None
+                r["launch_ms"] = avg_ms
+                r["launches_per_step"] = pk["launches"] / args.steps
+                return r
+
             dom = max(("basis", "h", "density"), key=lambda k: prof[k]["ms"])
-            pk = prof[dom]
-            avg_ms = pk["ms"] / max(1, pk["launches"])
-            per_launch_flops = pk["flops"] / max(1, pk["launches"])
-            per_launch_bytes = pk["bytes"] / max(1, pk["launches"])
-            if dom == "basis":
-                # FP32 pipe: 152 SMs x 128 lanes x 2 FLOP (FMA) per clock at the
-                # sampled maximum SM clock; the algorithmic count is ~30 FLOP
-                # per (point, function)
-                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
-                mhz = clk.summary().get("sm_max_mhz") or 2070.0
-                peak = fp32_alu_peak(torch, mhz)
-                roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                        "peak_note": "FP32 FMA issue rate: SMs x 128 lanes x 2 FLOP x %.0f MHz" % mhz}
-            elif args.precision == "fp64":
-                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
-                peak = fp64_gemm_peak(torch)
-                roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                        "peak_note": "measured FP64 GEMM (cuBLAS) on this GPU"}
-            else:
-                # BF16 products per algorithmic FLOP: split H 8, split density 6
-                products = ({"h": 8, "density": 6}[dom] if args.precision == "split_bf16" else 1)
-                ach = per_launch_flops / (avg_ms * 1e-3) / 1e12
-                peak = peaks["bf16_tflops_sustained"] / products
-                roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                        "peak_note": "%s sustained BF16 / %d BF16 products per algorithmic FLOP"
-                                     % (peak_src, products)}
-            roof["frac"] = roof["achieved"] / roof["peak"]
-            roof["traffic"] = traffic_for(dom)
-            roof["launch_ms"] = avg_ms
-            roof["launches_per_step"] = pk["launches"] / args.steps
+            roof = roofline(dom)
+            # the other kernel classes, for context (the line above is the dominant one)
+            roof_all = {k: {q: roofline(k)[q] for q in ("bound", "achieved", "peak", "unit", "frac")}
+                        for k in ("basis", "h", "density")}
         cpu = None
         if not args.no_cpu_baseline:
             p, dt, thr, nbs = oracle_sample(prob, D, args.ref_batches)
@@ -495,6 +502,7 @@ def main():
                           "graph": bool(args.graph), "plan_s": round(plan_s, 3)},
                "tflops": flops_step / (ms_max * 1e-3) / 1e12 if flops_step else None,
                "roofline": roof,
+               "roofline_by_kernel": roof_all,
                "cpu_baseline": cpu,
                "e2e": {"value": n_pts * world / (e2e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
