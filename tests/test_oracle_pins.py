@@ -291,3 +291,22 @@ def test_adjoint_matches_central_differences():
             xm[a, x] -= h
             fd = (L(xyz=xp) - L(xyz=xm)) / (2 * h)
             assert dR[a, x] == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(dR).max())
+
+
+def test_oracle_reproduces_its_regression_fixture():
+    """tests/golden/water_16x26_oracle.txt freezes the oracle's H, S and
+    density on a small water grid (written by tests/golden/make_golden.py);
+    the fixture itself satisfies tr(DS) = 10 (five doubly occupied orbitals)."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    ref = mg.read(os.path.join(here, "water_16x26_oracle.txt"))
+    prob, H, S, D, n = mg.water_case()
+    assert prob.n_pts == int(ref["n_points"][0])
+    np.testing.assert_allclose(H, ref["H"], rtol=1e-12, atol=1e-14 * np.abs(ref["H"]).max())
+    np.testing.assert_allclose(S, ref["S"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(n[:16], ref["n_first16"], rtol=1e-12, atol=1e-14)
+    assert np.trace(ref["D"] @ ref["S"]) == pytest.approx(10.0, rel=1e-12)
