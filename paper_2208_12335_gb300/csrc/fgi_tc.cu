@@ -422,6 +422,19 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
         }
         const float *pp = P.pts_dd + 6 * (B.pt0 + p);
         const float *aa = P.atom_dd + 6 * A.atom;
+        {
+            // beyond the largest cutoff of the atom's shells every value is
+            // zero: an FP32 distance (relative error ~1e-7) against the cutoff
+            // with a 1e-5 margin decides, without the double-float work
+            const float xf = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+            const float yf = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+            const float zf = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+            const float rc = (float)S.rcut * 1.00001f;
+            if (xf * xf + yf * yf + zf * zf > rc * rc) {
+                for (int f = f_lo; f < f_hi; f++) out[f * kPhiValStride] = make_float2(0.f, 0.f);
+                continue;
+            }
+        }
         const df x = df_sub(df{pp[0], pp[1]}, df{aa[0], aa[1]});
         const df y = df_sub(df{pp[2], pp[3]}, df{aa[2], aa[3]});
         const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
@@ -743,6 +756,7 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
             const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
             const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
             const float d = sqrtf(x * x + y * y + z * z);
+            if (d > (float)S.rcut * 1.00001f) continue;        // every shell is zero here
             const float inv_d = __frcp_rn(d);
             float mx = 0.f, sm = 0.f;
             for (int sh = 0; sh < S.n_shell; sh++) {
