@@ -1,14 +1,18 @@
 // Tensor-core path for sm_103a: basis evaluation into swizzled BF16 operand
-// images, the H contraction h_b = Phi_b^T diag(w v) Phi_b on tcgen05 with
-// FP64 atomic scatter, the D_b gather, and the density contraction
+// images, the H contraction h_b = Phi_b^T diag(w v) Phi_b on tcgen05 (or
+// s Psi_b^T Psi_b with Psi = Phi sqrt|w v| where w v has one sign s) with a
+// fixed-point scatter into H, the D_b gather, and the density contraction
 // n_p = sum_j (D_b Phi_b^T)_jp phi_j(p) on tcgen05.
 //
 // Precision: every value x entering a contraction is split into three BF16
-// terms x = x0 + x1 + x2 (round to nearest at each step, so |x - sum| is
-// about 2^-24 |x|); the six products of combined order <= 2 are accumulated
-// in FP32 in tensor memory, x0*y0 in its own accumulator and the five
-// smaller ones in a second; the two are combined in FP64 and every
-// cross-batch sum is FP64.  n_split = 1 keeps x0*y0 only (plain BF16).
+// terms x = x0 + x1 + x2: x0 a fixed-point digit on a power-of-two grid per
+// row (H) or per point (density), chosen so that every partial sum of
+// x0*y0 products is exact in FP32, and x1, x2 the BF16 split of the
+// remainder.  H accumulates the 8 products of combined order <= 3 except
+// x2*y2, the density the 6 of order <= 2; x0*y0 has its own FP32
+// accumulator in tensor memory, the others a second one.  Cross-batch sums:
+// H in 2^-40 fixed point (int64 atomics, deterministic), the density in
+// FP64.  n_split = 1 keeps x0*y0 only (plain BF16).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -511,9 +515,11 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 }
 
 // -------------------------------------------- basis -> operand images (K1)
-// CTA per (batch, 128-row block).  For each 64-point chunk: evaluate phi for
-// the block's rows into shared memory, then write the split planes of phi
-// (and of w v phi when v is given) as swizzled 16-byte units.
+// CTA per (batch, 128-row block).  A first FP32 pass takes the rows' maxima
+// and sums for the fixed-point grids; then, for each 32-point half chunk,
+// phi of the block's rows is evaluated into shared memory and the split
+// planes of psi = phi sqrt|w v| (batches where w v has one sign) or of phi
+// and w v phi (mixed signs) are written as swizzled 16-byte units.
 //
 // The radial factor N_lm u(d)/d^(l+1) -- shared by all angular points of a
 // radial shell, so its rounding would be systematic -- is evaluated in
