@@ -126,6 +126,9 @@ int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w
    h_sb_growth (the same two limits for the H path; defaults 400 points and
    1.25, so only small neighbouring batches merge).  A missing file
    means the defaults; a malformed or out-of-range value is FGI_ERR_ARG.
+   For experiments, the environment variables FGI_SB_POINTS,
+   FGI_SB_GROWTH, FGI_H_SB_POINTS, FGI_H_SB_GROWTH and FGI_TC_WAVE_MB
+   override the file's values when set.
    The paper has no counterpart for the settings (it prints no kernel). */
 int fgi_plan(fgi_ctx *ctx, fgi_precision precision, const char *tune_cache_path);
 
