@@ -236,12 +236,13 @@ enum {
    enable = 0 stops.  Not for use inside stream capture. */
 int fgi_profile(fgi_ctx *ctx, int enable);
 
-/* Totals over the recorded launches of one kernel class: number of
+/* Totals over the recorded launches of one kernel class: number of kernel
    launches, summed event time (ms), and the algorithmic FLOPs and bytes
-   those launches had to process (per batch: H P n (n+1) for the upper
-   triangle, density 2 P n^2 + 2 P n, scatter 16 bytes per stored upper
-   entry, with P points and n active functions).  Waits for the recorded
-   events. */
+   those launches had to process (per batch, with P points and n active
+   functions: H P n (n+1) for the upper triangle; density P n (n+1) + 2 P n
+   on the tensor-core paths, which use the upper block triangle of the
+   symmetric D, and 2 P n^2 + 2 P n on the FP64 path; scatter 16 bytes per
+   stored upper entry).  Waits for the recorded events. */
 int fgi_profile_read(fgi_ctx *ctx, int kind, int64_t *launches, double *ms, double *flops,
                      double *bytes);
 

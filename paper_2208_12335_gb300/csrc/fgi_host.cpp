@@ -37,6 +37,7 @@ struct ProfRec {
     int kind;
     cudaEvent_t a, b;
     double flops, bytes;
+    int kernels;                 // kernel launches inside the timed scope
 };
 
 struct Wave {
@@ -687,8 +688,9 @@ struct ProfScope {
     int kind;
     double flops, bytes;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(fgi_ctx *c_, cudaStream_t s_, int kind_, double f, double by)
-        : c(c_), s(s_), kind(kind_), flops(f), bytes(by)
+    int kernels;
+    ProfScope(fgi_ctx *c_, cudaStream_t s_, int kind_, double f, double by, int kernels_ = 1)
+        : c(c_), s(s_), kind(kind_), flops(f), bytes(by), kernels(kernels_)
     {
         if (!c->prof_on) return;
         while (c->ev_used + 2 > c->ev_pool.size()) {
@@ -707,7 +709,7 @@ struct ProfScope {
     {
         if (!a) return;
         cudaEventRecord(b, s);
-        c->recs.push_back(ProfRec{kind, a, b, flops, bytes});
+        c->recs.push_back(ProfRec{kind, a, b, flops, bytes, kernels});
     }
 };
 
@@ -1083,7 +1085,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
         Q.batches = c->tcd.d_sb;
         Q.act = c->tcd.d_sact;
         {
-            ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz);
+            ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz, 2);          // conversion of D and its bounds
             CUDA_TRY(c, tc_launch_to_df(c->tcd, Q, d, ws, c->d_sys_val0, c->d_sys_nnz, c->d_fn_sys, s));
         }
         for (const TcWave &w : c->tcd.waves) {
@@ -1095,7 +1097,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
                 ProfScope ps(c, s, 4, 0.0, w.g_bytes);
                 CUDA_TRY(c, tc_launch_gather_d(c->tcd, Q, w, 1.0, ws, n_split, s));
             }
-            ProfScope ps(c, s, 2, w.n_flops, w.n_bytes);
+            ProfScope ps(c, s, 2, w.n_flops, w.n_bytes, 2);        // contraction + per-block sums
             CUDA_TRY(c, tc_launch_density(c->tcd, Q, w, ws, n, n_split, s));
         }
     }
@@ -1201,7 +1203,7 @@ int fgi_profile_read(fgi_ctx *c, int kind, int64_t *launches, double *ms, double
         CUDA_TRY(c, cudaEventSynchronize(r.b));
         float e = 0.f;
         CUDA_TRY(c, cudaEventElapsedTime(&e, r.a, r.b));
-        n++;
+        n += r.kernels;
         t += e;
         f += r.flops;
         by += r.bytes;
