@@ -254,3 +254,36 @@ def test_h_sign_changing_potential(fgi, si64_sub, precision, tol):
     err = np.max(np.abs(h - ref))
     bound = TOL_FP64 * np.abs(Hs).max() if tol is None else tol
     assert err <= bound, (precision, err, np.abs(Hs).max())
+
+
+@pytest.fixture(scope="module")
+def one_function_atoms():
+    """60 atoms with a single s function each (a minimal basis), so that a
+    128-function block of H spans more atoms than the H scatter's per-tile
+    pair table holds and its fallback path runs."""
+    rc = 3.0 * W.BOHR_PER_ANG
+    rad = W.make_radial(W.RadialSpec(0, (0.9,), (1.0,), rc, rc - 1.0 * W.BOHR_PER_ANG, 1000))
+    species = [W.Species("X", 1.0, [0])]
+    rng = np.random.default_rng(31)
+    xyz = []
+    while len(xyz) < 150:
+        p = rng.uniform(-6.0, 6.0, 3)
+        if all(np.linalg.norm(p - q) > 1.6 for q in xyz):
+            xyz.append(p)
+    xyz = np.array(xyz)
+    prob = W.build_problem("minimal", [rad], species, [(np.zeros(len(xyz), dtype=np.int32), xyz)],
+                           lambda sp: (8, 26), 7, (200, 50, None))
+    B = O.system_basis(prob)
+    return prob, B, O.h_matrix(B, prob.pts, prob.w, prob.v)
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_minimal_basis_many_atoms_per_block(fgi, one_function_atoms, precision, tol):
+    prob, B, H = one_function_atoms
+    assert B.n_fn == 150                             # one function per atom: a tile spans up to 128 atoms
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()
+    err = np.max(np.abs(h - stored(ctx, H)))
+    bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(H).max())
