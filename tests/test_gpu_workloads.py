@@ -162,3 +162,27 @@ def test_autotuner_writes_settings_that_plan_and_keep_parity(fgi, tmp_path):
     ctx.sync()
     r, c = rows_cols(ctx)
     assert np.max(np.abs(h - H[r, c])) <= 1e-7
+
+
+def test_many_small_waves_give_the_same_results(fgi, tmp_path):
+    """A wave size of 8 MiB splits the Si64 sub-grid into many waves (the
+    operand images of one wave at a time); H (fixed-point sums) and the
+    density (per-point sums in block order) must come out bitwise the same
+    as with one wave."""
+    full = W.si64()
+    ids = np.sort(np.random.default_rng(5).choice(full.n_batch, size=48, replace=False))
+    prob = full.subgrid(ids)
+    small = tmp_path / "small_waves.txt"
+    small.write_text("wave_mb 8\n")
+    out = []
+    for path in (None, str(small)):
+        ctx = fgi.Context(0).load(prob, "split_bf16", tune_path=path)
+        nnz = ctx.sizes()[1]
+        d = dev(np.random.default_rng(8).standard_normal(nnz) * 0.05)
+        h = ctx.integrate_h(dev(prob.v)).clone()
+        n, _ = ctx.density(d)
+        ctx.sync()
+        out.append((h.cpu(), n.clone().cpu(), ctx.workspace_size()))
+    assert out[1][2] < out[0][2]                      # smaller waves, smaller workspace
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
