@@ -287,3 +287,31 @@ def test_h_minimal_basis_many_atoms_per_block(fgi, one_function_atoms, precision
     err = np.max(np.abs(h - stored(ctx, H)))
     bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
     assert err <= bound, (precision, err, np.abs(H).max())
+
+
+def test_split_context_reports_nonfinite_potential_and_recovers(fgi, water):
+    prob, _, H, _ = water
+    ctx = fgi.Context(0).load(prob, "split_bf16")
+    v = prob.v.copy()
+    v[5] = np.inf
+    ctx.integrate_h(dev(v))
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.sync()
+    assert e.value.code == -6
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()                                    # status word was cleared
+    assert np.max(np.abs(h - stored(ctx, H))) <= TOL_SPLIT_H
+
+
+def test_adjoint_of_a_split_context_is_the_fp64_adjoint(fgi, water):
+    prob, _, _, _ = water
+    g = dev(W.rng_for(0, W.PURPOSE_G).standard_normal(fgi.Context(0).load(prob, "fp64").sizes()[1]))
+    res = []
+    for precision in ("fp64", "split_bf16"):
+        ctx = fgi.Context(0).load(prob, precision)
+        dv, dR = ctx.adjoint(g, dev(prob.v))
+        ctx.sync()
+        res.append((dv.cpu(), dR.cpu()))
+    assert torch.equal(res[0][0], res[1][0])          # dv: per-point sums, same order
+    # dR: FP64 atomics over batches, so the order of additions may differ
+    assert torch.allclose(res[0][1], res[1][1], rtol=0, atol=1e-12 * res[0][1].abs().max().item())
