@@ -315,3 +315,37 @@ def test_adjoint_of_a_split_context_is_the_fp64_adjoint(fgi, water):
     assert torch.equal(res[0][0], res[1][0])          # dv: per-point sums, same order
     # dR: FP64 atomics over batches, so the order of additions may differ
     assert torch.allclose(res[0][1], res[1][1], rtol=0, atol=1e-12 * res[0][1].abs().max().item())
+
+
+@pytest.fixture(scope="module")
+def spdf_molecule():
+    """Three atoms of one species with s, p, d and f shells (16 functions per
+    atom), so that every angular momentum the library supports (l <= 3) goes
+    through both GPU paths."""
+    rc = 4.0 * W.BOHR_PER_ANG
+    ron = rc - 1.0 * W.BOHR_PER_ANG
+    specs = [W.RadialSpec(l, (0.5 + 0.15 * l, 1.4), (1.0, -0.25), rc, ron, 2000) for l in range(4)]
+    radials = [W.make_radial(s) for s in specs]
+    species = [W.Species("Y", 4.0, [0, 1, 2, 3])]
+    xyz = np.array([[0.0, 0.0, 0.0], [2.3, 0.4, -0.3], [-0.8, 2.1, 1.1]])
+    prob = W.build_problem("spdf", radials, species, [(np.zeros(3, dtype=np.int32), xyz)],
+                           lambda sp: (24, 50), 8, (200, 50, None))
+    B = O.system_basis(prob)
+    return prob, B, O.h_matrix(B, prob.pts, prob.w, prob.v)
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_and_density_with_f_functions(fgi, spdf_molecule, precision, tol):
+    prob, B, H = spdf_molecule
+    assert B.n_fn == 48
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    D, _ = W.density_matrix_occ(B.n_fn, 12, np.random.default_rng(12))
+    n, _ = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    err = np.max(np.abs(h - stored(ctx, H)))
+    bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(H).max())
+    nref = O.density(B, prob.pts, D)
+    rel = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
+    assert rel <= {"fp64": 1e-12, "split_bf16": TOL_SPLIT_N, "bf16": 1e-2}[precision], rel
