@@ -349,3 +349,22 @@ def test_h_and_density_with_f_functions(fgi, spdf_molecule, precision, tol):
     nref = O.density(B, prob.pts, D)
     rel = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
     assert rel <= {"fp64": 1e-12, "split_bf16": TOL_SPLIT_N, "bf16": 1e-2}[precision], rel
+
+
+def test_batches_of_the_maximum_size(fgi, water):
+    """Water's points cut into batches of exactly 1024 points (the largest a
+    batch may hold; the last one shorter): split H and density still meet
+    the stated tolerances."""
+    prob, B, H, _ = water
+    off = np.concatenate([np.arange(0, prob.n_pts, 1024), [prob.n_pts]]).astype(np.int64)
+    big = W.Problem("water-1024", prob.radials, prob.species, prob.atom_off, prob.atom_species, prob.atom_xyz,
+                    prob.pts, prob.w, off, np.zeros(len(off) - 1, dtype=np.int32), prob.v)
+    assert np.diff(off)[:-1].min() == 1024
+    ctx = fgi.Context(0).load(big, "split_bf16")
+    h = ctx.integrate_h(dev(big.v)).cpu().numpy()
+    D, _ = W.density_matrix_occ(B.n_fn, 3, np.random.default_rng(2))
+    n, _ = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    assert np.max(np.abs(h - stored(ctx, H))) <= TOL_SPLIT_H
+    nref = O.density(B, big.pts, D)
+    assert np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref) <= TOL_SPLIT_N
