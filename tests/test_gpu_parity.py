@@ -368,3 +368,31 @@ def test_batches_of_the_maximum_size(fgi, water):
     assert np.max(np.abs(h - stored(ctx, H))) <= TOL_SPLIT_H
     nref = O.density(B, big.pts, D)
     assert np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref) <= TOL_SPLIT_N
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_far_batch_without_functions_and_one_point_batch(fgi, water, precision):
+    """Edge cases of the grid: an extra batch of points far from every atom
+    (no active functions: zero density, no H contribution) and a batch of a
+    single point."""
+    prob, B, H, _ = water
+    far = np.array([[40.0, 0.0, 0.0], [40.5, 0.3, 0.0], [40.2, -0.4, 0.1]])
+    one = prob.pts[:1] + 0.01
+    pts = np.concatenate([prob.pts, far, one])
+    w = np.concatenate([prob.w, [0.1, 0.2, 0.3], [0.05]])
+    v = np.concatenate([prob.v, [-0.01, -0.02, -0.03], [prob.v[0]]])
+    off = np.concatenate([prob.batch_off, [prob.n_pts + 3, prob.n_pts + 4]]).astype(np.int64)
+    edge = W.Problem("water-edge", prob.radials, prob.species, prob.atom_off, prob.atom_species, prob.atom_xyz,
+                     pts, w, off, np.zeros(len(off) - 1, dtype=np.int32), v)
+    Href = O.h_matrix(B, pts, w, v)
+    ctx = fgi.Context(0).load(edge, precision)
+    h = ctx.integrate_h(dev(v)).cpu().numpy()
+    D, _ = W.density_matrix_occ(B.n_fn, 3, np.random.default_rng(2))
+    n, _ = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    n = n.cpu().numpy()
+    tol = TOL_FP64 * np.abs(Href).max() if precision == "fp64" else TOL_SPLIT_H
+    assert np.max(np.abs(h - stored(ctx, Href))) <= tol
+    assert np.all(n[prob.n_pts:prob.n_pts + 3] == 0.0)
+    nref = O.density(B, pts[-1:], D)[0]
+    assert n[-1] == pytest.approx(nref, rel=1e-7 if precision != "fp64" else 1e-12)
