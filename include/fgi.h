@@ -231,6 +231,15 @@ enum {
     FGI_KERNEL_OTHER = 4      /* reductions and traces */
 };
 
+/* Failure-path self-test: enqueues one small kernel whose bounded wait on
+   a barrier that nothing completes runs out after about 2 s, as the
+   pipelined kernels' waits do when a stage never arrives.  The device status
+   word records the time-out; the next fgi_sync reports FGI_ERR_TIMEOUT and
+   clears it, and the context stays usable.  No fault and no hang: for
+   testing error handling.  Needs a planned context.  The paper has no
+   counterpart (it describes no kernels). */
+int fgi_selftest_wait_timeout(fgi_ctx *ctx, void *stream);
+
 /* Launch profile: enable = 1 clears the record and starts timing every
    launch of the library's kernels with CUDA events on the call's stream;
    enable = 0 stops.  Not for use inside stream capture. */

@@ -1171,6 +1171,15 @@ int fgi_sync(fgi_ctx *c, void *stream)
     return FGI_OK;
 }
 
+int fgi_selftest_wait_timeout(fgi_ctx *c, void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    CUDA_TRY(c, tc_launch_wait_selftest(c->d_status, (cudaStream_t)stream));
+    return FGI_OK;
+}
+
 int fgi_profile(fgi_ctx *c, int enable)
 {
     int rc = check_compute(c);

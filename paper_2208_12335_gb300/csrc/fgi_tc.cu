@@ -828,7 +828,6 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
 // The bits below 2^-40 are dropped toward zero (f = +1/2 exactly saturates
 // the low word, an error of one unit).  |v| must stay below 2^22; larger or
 // non-finite values set *bad.
-constexpr int kFixBits = 40;
 
 __device__ __forceinline__ long long f32_to_fix(float v, bool &bad)
 {
@@ -1864,6 +1863,28 @@ cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_density_sum<<<(unsigned)w.nd, 128, 0, s>>>(P, t.d_batches, t.d_items + w.d0, part, n);
+    return cudaGetLastError();
+}
+
+// Self-test of the failure path: one CTA waits on an mbarrier that nothing
+// completes.  The bounded wait gives up after kWaitLimitNs and records the
+// time-out in the status word, as a stalled pipeline would; no fault, no hang.
+__global__ void k_wait_selftest(int *status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_a(&bar, 0, status, &abort_flag);
+}
+
+cudaError_t tc_launch_wait_selftest(int *status, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(status);
     return cudaGetLastError();
 }
 

@@ -101,4 +101,7 @@ cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &
 cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
                               double *n, int n_split, cudaStream_t s);
 
+// failure-path self-test: a bounded wait that runs out (status time-out)
+cudaError_t tc_launch_wait_selftest(int *status, cudaStream_t s);
+
 }  // namespace fgi

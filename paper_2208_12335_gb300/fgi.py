@@ -27,7 +27,7 @@ SYMBOLS = ["fgi_create", "fgi_destroy", "fgi_last_error", "fgi_add_radial", "fgi
            "fgi_set_systems", "fgi_set_grid", "fgi_plan", "fgi_set_precision", "fgi_get_sizes",
            "fgi_get_system", "fgi_get_pattern", "fgi_workspace_size", "fgi_integrate_h",
            "fgi_density", "fgi_adjoint", "fgi_trace", "fgi_sync", "fgi_profile",
-           "fgi_profile_read", "fgi_integrate_h_static", "fgi_get_batch_work"]
+           "fgi_profile_read", "fgi_integrate_h_static", "fgi_get_batch_work", "fgi_selftest_wait_timeout"]
 KERNEL_KINDS = {"basis": 0, "h": 1, "density": 2, "adjoint": 3, "other": 4}
 
 
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgi_profile_read": ([P, I, C.POINTER(I64), C.POINTER(D), C.POINTER(D), C.POINTER(D)], I),
         "fgi_integrate_h_static": ([P, P, P, I, P], I),
         "fgi_get_batch_work": ([P, I64, P, P], I),
+        "fgi_selftest_wait_timeout": ([P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -280,6 +281,11 @@ class Context:
 
     def sync(self, stream=None):
         self._check(self._lib.fgi_sync(self._h, _stream(stream)))
+
+    def selftest_wait_timeout(self, stream=None):
+        """Enqueue a bounded device wait that runs out (about 2 s); the next
+        sync() raises FGIError with code FGI_ERR_TIMEOUT."""
+        self._check(self._lib.fgi_selftest_wait_timeout(self._h, _stream(stream)))
 
     def profile(self, enable: bool = True):
         self._check(self._lib.fgi_profile(self._h, int(bool(enable))))

@@ -158,6 +158,7 @@ def test_host_only_context_refuses_compute_and_checks_precision(fgi, water):
     lib = fgi.lib()
     assert lib.fgi_sync(ctx._h, None) == -2
     assert lib.fgi_density(ctx._h, None, None, None, None, 0, None) == -2
+    assert lib.fgi_selftest_wait_timeout(ctx._h, None) == -2
     with pytest.raises(fgi.FGIError):
         ctx.set_precision(7)
     ctx.set_precision("split_bf16")
