@@ -7,8 +7,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fgi_internal.h"
@@ -53,6 +55,43 @@ struct Slot {                     // an array inside the device arena
     size_t off = 0, n = 0;
 };
 
+// Allocator whose value-less construct leaves the element uninitialised, so
+// that resize() of a large buffer does not zero it on one thread before a
+// parallel loop fills it (the fill is then also the pages' first touch).
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <typename U>
+    NoInitAlloc(const NoInitAlloc<U> &) noexcept {}
+    template <typename U>
+    void construct(U *p) noexcept
+    {
+        ::new ((void *)p) U;
+    }
+    template <typename U, typename... A>
+    void construct(U *p, A &&...a)
+    {
+        ::new ((void *)p) U(std::forward<A>(a)...);
+    }
+};
+
+template <typename T>
+using BigVec = std::vector<T, NoInitAlloc<T>>;
+
+// dst[0..n) = src[0..n), in parallel chunks
+template <typename T>
+void par_copy(T *dst, const T *src, int64_t n)
+{
+    const int64_t chunk = 1 << 16;
+#pragma omp parallel for schedule(static)
+    for (int64_t c0 = 0; c0 < n; c0 += chunk)
+        std::memcpy(dst + c0, src + c0, sizeof(T) * (size_t)std::min(chunk, n - c0));
+}
+
 }  // namespace
 
 struct fgi_ctx {
@@ -68,7 +107,7 @@ struct fgi_ctx {
     bool have_systems = false;
     // grid
     int64_t n_pts = 0;
-    std::vector<double> pts, w;
+    BigVec<double> pts, w;
     std::vector<int64_t> batch_off;
     std::vector<int> batch_sys;
     bool have_grid = false;
@@ -383,6 +422,11 @@ int build_plan(fgi_ctx *c, const char *tune_path)
 
     // batches, active entries, FP64 waves and work items
     c->act.clear();
+    {
+        size_t n_act = 0;
+        for (int64_t b = 0; b < nb; b++) n_act += active[b].size();
+        c->act.reserve(n_act);
+    }
     c->batches_f64.assign(nb, DevBatch{});
     for (int64_t b = 0; b < nb; b++) {
         DevBatch &B = c->batches_f64[b];
@@ -425,6 +469,13 @@ int build_plan(fgi_ctx *c, const char *tune_path)
             c->waves.push_back(wv);
         }
         size_t max_elems = 0;
+        size_t n_items = 0;
+        for (int64_t b = 0; b < nb; b++) {
+            const long long nt = (c->batches_f64[b].nfn + 63) / 64;
+            n_items += (size_t)(nt * (nt + 1) / 2);
+            if (c->batches_f64[b].nfn > 0) n_items += (size_t)((c->batches_f64[b].np + 63) / 64);
+        }
+        c->items.reserve(n_items);
         for (Wave &w : c->waves) {
             w.it0 = (long long)c->items.size();
             for (int b = w.b0; b < w.b0 + w.nb; b++) {
@@ -489,9 +540,11 @@ int build_plan(fgi_ctx *c, const char *tune_path)
             coef_dd[8 * k + q] = hi;
             coef_dd[8 * k + 4 + q] = (float)(coef[4 * k + q] - (double)hi);
         }
-    auto to_dd = [](const std::vector<double> &xyz) {
-        std::vector<float> out(xyz.size() * 2);
-        for (size_t i = 0; i < xyz.size() / 3; i++)
+    // coordinates as double-floats: per point (x_hi, x_lo, y_hi, y_lo, z_hi, z_lo)
+    auto to_dd = [](const double *xyz, int64_t n) {
+        BigVec<float> out(6 * (size_t)n);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++)
             for (int k = 0; k < 3; k++) {
                 const float hi = (float)xyz[3 * i + k];
                 out[6 * i + 2 * k] = hi;
@@ -499,7 +552,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
             }
         return out;
     };
-    std::vector<float> pts_dd = to_dd(c->pts), atom_dd = to_dd(c->atom_xyz);
+    BigVec<float> pts_dd = to_dd(c->pts.data(), c->n_pts);
+    BigVec<float> atom_dd = to_dd(c->atom_xyz.data(), (int64_t)(c->atom_xyz.size() / 3));
     std::vector<DevSpecies> dsp;
     std::vector<int> shell_rad;
     // species whose shells share one knot grid also get their coefficients
@@ -533,7 +587,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         dsp.push_back(d);
     }
     if (scoef.empty()) scoef.assign(8, 0.f);
-    std::vector<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
+    BigVec<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < c->n_pts; p++) {
         px[p] = c->pts[3 * p];
         py[p] = c->pts[3 * p + 1];
@@ -919,13 +974,19 @@ int fgi_set_grid(fgi_ctx *c, int64_t n_pts, const double *xyz, const double *w, 
                            (long long)np, kMaxBatchPoints);
         if (batch_sys[b] < 0) return set_err(c, FGI_ERR_ARG, "grid: bad batch_sys");
     }
+    int64_t first_bad = n_pts;   // the lowest index of a non-finite point
+#pragma omp parallel for schedule(static) reduction(min : first_bad)
     for (int64_t p = 0; p < n_pts; p++)
         if (!std::isfinite(w[p]) || !std::isfinite(xyz[3 * p]) || !std::isfinite(xyz[3 * p + 1]) ||
             !std::isfinite(xyz[3 * p + 2]))
-            return set_err(c, FGI_ERR_NONFINITE, "grid: point %lld not finite", (long long)p);
+            first_bad = std::min(first_bad, p);
+    if (first_bad < n_pts)
+        return set_err(c, FGI_ERR_NONFINITE, "grid: point %lld not finite", (long long)first_bad);
     c->n_pts = n_pts;
-    c->pts.assign(xyz, xyz + 3 * n_pts);
-    c->w.assign(w, w + n_pts);
+    c->pts.resize(3 * (size_t)n_pts);
+    c->w.resize((size_t)n_pts);
+    par_copy(c->pts.data(), xyz, 3 * n_pts);
+    par_copy(c->w.data(), w, n_pts);
     c->batch_off.assign(batch_off, batch_off + n_batch + 1);
     c->batch_sys.assign(batch_sys, batch_sys + n_batch);
     c->have_grid = true;

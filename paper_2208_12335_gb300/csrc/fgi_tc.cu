@@ -1676,6 +1676,15 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         off += foot[b];
     }
     finish_wave(n_sb);
+    {
+        size_t n_items = 0;   // the six lists below, for one allocation
+        for (int b = 0; b < n_sb; b++) {
+            if (t.sb[b].np <= 0 || t.sb[b].nfn <= 0) continue;
+            const size_t nrb = (size_t)t.batches[b].nrb, nca = (size_t)t.batches[b].nc_alloc;
+            n_items += 2 * nrb + nrb * (nrb + 1) / 2 + nca + nca / 2 + nrb * (nca / 2);
+        }
+        t.items.reserve(n_items);
+    }
     for (TcWave &wv : t.waves) {
         // longest first: the wave's batches by contraction cost P n^2, each
         // batch's items kept together (they share image tiles in L2); the
