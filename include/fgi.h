@@ -153,6 +153,27 @@ int fgi_get_system(fgi_ctx *ctx, int sys, int64_t *fn0, int64_t *n_fn, int64_t *
    FGI_ERR_ARG if n_batch differs from the planned batch count. */
 int fgi_get_batch_work(fgi_ctx *ctx, int64_t n_batch, int64_t *points, int32_t *n_active_fns);
 
+/* The tensor-core schedule (host, after fgi_plan) of the H integration
+   (which = 0) or of the density (which = 1).  Consecutive batches of one
+   system are merged into super-batches: a batch joins while the merged
+   points stay within the point limit and the union of active functions
+   within the growth limit times the largest member's (the tune-file keys
+   h_sb_points / h_sb_growth and density_sb_points / density_sb_growth).
+   Consecutive super-batches form waves whose operand images fit the wave
+   budget (wave_mb); each wave's tile lists take its super-batches longest
+   first by P n^2 (stable for ties), and those without points or functions
+   get no tiles.  Outputs (every pointer may be NULL; query the counts
+   first):
+     *n_super, *n_waves                 counts
+     sb_first_batch[n_super + 1]        super-batch s = batches [first[s], first[s+1])
+     sb_points[n_super], sb_fns[n_super]  its points and active functions
+     wave_first_sb[n_waves + 1]         wave k = super-batches [first[k], first[k+1])
+     sb_rank[n_super]                   position in its wave's tile lists, -1 if none
+   The paper has no counterpart (it prints no kernel or schedule).
+   FGI_ERR_ARG for another `which`. */
+int fgi_get_schedule(fgi_ctx *ctx, int which, int64_t *n_super, int64_t *n_waves, int64_t *sb_first_batch,
+                     int32_t *sb_points, int32_t *sb_fns, int64_t *wave_first_sb, int32_t *sb_rank);
+
 /* CSR pattern of system `sys` (host arrays owned by the context, valid until
    the next fgi_plan/fgi_set_*): rowptr[n_fn(sys)+1] (relative to val0(sys))
    and col[nnz(sys)] (function index within the system). */

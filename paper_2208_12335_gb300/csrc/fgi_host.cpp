@@ -1068,6 +1068,30 @@ int fgi_get_batch_work(fgi_ctx *c, int64_t n_batch, int64_t *points, int32_t *n_
     return FGI_OK;
 }
 
+int fgi_get_schedule(fgi_ctx *c, int which, int64_t *n_super, int64_t *n_waves, int64_t *sb_first_batch,
+                     int32_t *sb_points, int32_t *sb_fns, int64_t *wave_first_sb, int32_t *sb_rank)
+{
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (which != 0 && which != 1) return set_err(c, FGI_ERR_ARG, "which must be 0 (H) or 1 (density)");
+    const TcPlan &t = which == 0 ? c->tc : c->tcd;
+    const int64_t ns = (int64_t)t.sb.size(), nw = (int64_t)t.waves.size();
+    if (n_super) *n_super = ns;
+    if (n_waves) *n_waves = nw;
+    for (int64_t s = 0; s < ns; s++) {
+        if (sb_points) sb_points[s] = t.sb[s].np;
+        if (sb_fns) sb_fns[s] = t.sb[s].nfn;
+        if (sb_rank) sb_rank[s] = t.sb_rank[s];
+    }
+    if (sb_first_batch)
+        for (int64_t s = 0; s <= ns; s++) sb_first_batch[s] = t.sb_first[s];
+    if (wave_first_sb) {
+        for (int64_t k = 0; k < nw; k++) wave_first_sb[k] = t.waves[k].b0;
+        wave_first_sb[nw] = ns;
+    }
+    return FGI_OK;
+}
+
 int fgi_get_pattern(fgi_ctx *c, int sys, int64_t *nnz, const int64_t **rowptr, const int **col)
 {
     int rc = check_ready(c);

@@ -1570,9 +1570,11 @@ static void build_super_batches(TcPlan &t, const TcPlanInput &in, int sb_points,
 {
     t.sb.clear();
     t.sact.clear();
+    t.sb_first.clear();
     std::vector<int> uni, tmp;
     int b = 0;
     while (b < in.n_batch) {
+        t.sb_first.push_back(b);
         const DevBatch &B0 = in.batches[b];
         uni.clear();
         for (int e = 0; e < B0.n_act; e++) uni.push_back(in.act[B0.act0 + e].atom);
@@ -1614,6 +1616,7 @@ static void build_super_batches(TcPlan &t, const TcPlanInput &in, int sb_points,
         t.sb.push_back(S);
         b = b2;
     }
+    t.sb_first.push_back(in.n_batch);
 }
 
 int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
@@ -1622,6 +1625,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
     build_super_batches(t, in, std::min(in.sb_points, kMaxBatchPoints), std::max(1.0, in.sb_growth));
     const int n_sb = (int)t.sb.size();
     t.batches.assign(n_sb, TcBatch{});
+    t.sb_rank.assign(n_sb, -1);
     t.items.clear();
     t.waves.clear();
     size_t cap = (size_t)24 << 30;   // workloads up to ~24 GB of operand images run as one wave
@@ -1694,6 +1698,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
             if (t.sb[b].np > 0 && t.sb[b].nfn > 0) ord.push_back(b);
         auto cost = [&](int b) { return (double)t.sb[b].np * t.sb[b].nfn * t.sb[b].nfn; };
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        for (size_t r = 0; r < ord.size(); r++) t.sb_rank[ord[r]] = (int)r;
         wv.phi0 = (long long)t.items.size();
         for (int b : ord)
             for (int I = 0; I < t.batches[b].nrb; I++) t.items.push_back(WorkItem{b, (short)I, 0});

@@ -68,6 +68,8 @@ struct TcPlan {
     int num_sms = 1;                     // persistent grids: one CTA per SM
     std::vector<DevBatch> sb;            // super-batches (points, union of active atoms)
     std::vector<DevAct> sact;            // their active-atom entries
+    std::vector<int> sb_first;           // first input batch of each super-batch (+ n_batch at the end)
+    std::vector<int> sb_rank;            // position in its wave's tile lists (-1: no tiles)
     const DevBatch *d_sb = nullptr;
     const DevAct *d_sact = nullptr;
     std::vector<TcBatch> batches;        // per super-batch image geometry

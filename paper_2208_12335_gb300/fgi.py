@@ -27,7 +27,8 @@ SYMBOLS = ["fgi_create", "fgi_destroy", "fgi_last_error", "fgi_add_radial", "fgi
            "fgi_set_systems", "fgi_set_grid", "fgi_plan", "fgi_set_precision", "fgi_get_sizes",
            "fgi_get_system", "fgi_get_pattern", "fgi_workspace_size", "fgi_integrate_h",
            "fgi_density", "fgi_adjoint", "fgi_trace", "fgi_sync", "fgi_profile",
-           "fgi_profile_read", "fgi_integrate_h_static", "fgi_get_batch_work", "fgi_selftest_wait_timeout"]
+           "fgi_profile_read", "fgi_integrate_h_static", "fgi_get_batch_work", "fgi_selftest_wait_timeout",
+           "fgi_get_schedule"]
 KERNEL_KINDS = {"basis": 0, "h": 1, "density": 2, "adjoint": 3, "other": 4}
 
 
@@ -67,6 +68,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgi_integrate_h_static": ([P, P, P, I, P], I),
         "fgi_get_batch_work": ([P, I64, P, P], I),
         "fgi_selftest_wait_timeout": ([P, P], I),
+        "fgi_get_schedule": ([P, I, C.POINTER(I64), C.POINTER(I64), P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +210,23 @@ class Context:
         nfn = np.zeros(nb, np.int32)
         self._check(self._lib.fgi_get_batch_work(self._h, nb, _ptr(pts), _ptr(nfn)))
         return pts, nfn
+
+    def schedule(self, which: str = "h"):
+        """The tensor-core schedule of the H integration ("h") or the density
+        ("density"): dict of sb_first_batch [n_super+1], sb_points, sb_fns,
+        wave_first_sb [n_waves+1] and sb_rank (position in the wave's tile
+        lists, -1 without tiles)."""
+        w = {"h": 0, "density": 1}[which]
+        ns, nw = C.c_int64(), C.c_int64()
+        self._check(self._lib.fgi_get_schedule(self._h, w, C.byref(ns), C.byref(nw),
+                                               None, None, None, None, None))
+        out = dict(sb_first_batch=np.zeros(ns.value + 1, np.int64), sb_points=np.zeros(ns.value, np.int32),
+                   sb_fns=np.zeros(ns.value, np.int32), wave_first_sb=np.zeros(nw.value + 1, np.int64),
+                   sb_rank=np.zeros(ns.value, np.int32))
+        self._check(self._lib.fgi_get_schedule(self._h, w, C.byref(ns), C.byref(nw), _ptr(out["sb_first_batch"]),
+                                               _ptr(out["sb_points"]), _ptr(out["sb_fns"]),
+                                               _ptr(out["wave_first_sb"]), _ptr(out["sb_rank"])))
+        return out
 
     def pattern(self, s: int = 0):
         nnz = C.c_int64()
