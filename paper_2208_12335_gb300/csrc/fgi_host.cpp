@@ -380,6 +380,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t b = 0; b < nb; b++) {
         const int64_t p0 = c->batch_off[b], p1 = c->batch_off[b + 1];
+        if (p1 == p0) continue;   // an empty batch has no active atoms
         const int s = c->batch_sys[b];
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
         for (int64_t p = p0; p < p1; p++)
