@@ -376,8 +376,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     // active atoms per batch
     const int64_t nb = (int64_t)c->batch_sys.size();
     std::vector<std::vector<int>> active(nb);
-    bool too_many = false;
-#pragma omp parallel for schedule(dynamic, 16)
+    int too_many = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : too_many)
     for (int64_t b = 0; b < nb; b++) {
         const int64_t p0 = c->batch_off[b], p1 = c->batch_off[b + 1];
         if (p1 == p0) continue;   // an empty batch has no active atoms
@@ -415,7 +415,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
                 nfn_b += c->atom_nfn[a];
             }
         }
-        if (nfn_b > kMaxBatchFns) too_many = true;
+        if (nfn_b > kMaxBatchFns) too_many = 1;
     }
     if (too_many)
         return set_err(c, FGI_ERR_UNSUPPORTED, "a batch has more than %d active functions; use smaller batches",

@@ -238,3 +238,25 @@ def test_system_problem_extracts_one_molecule(fgi):
         rp_j, col_j = joint.pattern(s)
         rp_a, col_a = alone.pattern(0)
         assert np.array_equal(rp_j, rp_a) and np.array_equal(col_j, col_a)
+
+
+def test_batch_beyond_the_function_limit_is_refused(fgi, water):
+    """64 atoms of 140 functions each (twenty f shells) all reach one batch:
+    8960 active functions exceed the per-batch limit of 8192, which the
+    plan reports instead of building tiles it cannot hold."""
+    ctx = host_ctx(fgi, water)
+    r = water.radials[0]
+    rid = ctx.add_radial(3, r.h, r.coef)
+    sp = ctx.add_species(1.0, [rid] * 20)
+    g = np.arange(4, dtype=np.float64)
+    xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    ctx.set_systems([0, 64], np.full(64, sp, np.int32), xyz)
+    pts = 1.5 + 0.1 * np.random.default_rng(0).standard_normal((10, 3))
+    ctx.set_grid(pts, np.ones(10), [0, 10], [0])
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("split_bf16")
+    assert e.value.code == -7
+    # 58 atoms (8120 functions) are within the limit
+    ctx.set_systems([0, 58], np.full(58, sp, np.int32), xyz[:58])
+    ctx.plan("split_bf16")
+    assert ctx.batch_work()[1][0] == 58 * 140
