@@ -1,0 +1,43 @@
+"""bench.py's host-side helpers (CPU): the clock summary that decides whether
+a run is kept, and the traffic record keyed to the kernel source."""
+import json
+
+import bench
+
+
+def test_clock_summary_median_max_and_throttle_reasons():
+    s = bench.ClockSampler(0)
+    ok = "0, {sm}, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, {cap}"
+    s.lines = [ok.format(sm=m, cap="Not Active") for m in (2070, 2055, 2040)]
+    s.lines += [ok.format(sm=1980, cap="Active"), "garbage", "0, [N/A], 2070, 1, 0, a, b, c, d"]
+    out = s.summary()
+    assert out["sm_mhz"] == 2047.5 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+    hot = "0, 1500, 2070, 1300, 0x48, Not Active, Active, Not Active, Not Active"
+    s.lines = [hot]
+    assert s.summary()["reasons"] == ["hw_thermal_slowdown"]
+    s.lines = []
+    assert s.summary()["sm_mhz"] is None
+
+
+def test_traffic_record_only_for_the_current_kernel_source(tmp_path, monkeypatch):
+    root = tmp_path
+    (root / "profiles").mkdir()
+    (root / "paper_2208_12335_gb300" / "csrc").mkdir(parents=True)
+    src = root / "paper_2208_12335_gb300" / "csrc" / "k.cu"
+    src.write_bytes(b"kernel source v1\n")
+    import hashlib
+    h = hashlib.sha256(b"kernel source v1\n").hexdigest()[:16]
+    rec = {"h": {"source": "k.cu", "source_sha256_16": h, "dram_bytes_per_launch": 123.0}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.traffic_for("h") == 123.0
+    assert bench.traffic_for("density") is None
+    src.write_bytes(b"kernel source v2\n")                 # the kernel changed since the capture
+    assert bench.traffic_for("h") is None
+
+
+def test_measured_peaks_file_is_read():
+    peaks, kind = bench.measured_peaks()
+    assert kind in ("measured", "fallback")
+    assert peaks["hbm_gbs"] > 0 and peaks["bf16_tflops"] > 0
