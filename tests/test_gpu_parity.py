@@ -373,15 +373,15 @@ def test_batches_of_the_maximum_size(fgi, water):
 @pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
 def test_far_batch_without_functions_and_one_point_batch(fgi, water, precision):
     """Edge cases of the grid: an extra batch of points far from every atom
-    (no active functions: zero density, no H contribution) and a batch of a
-    single point."""
+    (no active functions: zero density, no H contribution), a batch of a
+    single point, and empty batches (first, and between the two)."""
     prob, B, H, _ = water
     far = np.array([[40.0, 0.0, 0.0], [40.5, 0.3, 0.0], [40.2, -0.4, 0.1]])
     one = prob.pts[:1] + 0.01
     pts = np.concatenate([prob.pts, far, one])
     w = np.concatenate([prob.w, [0.1, 0.2, 0.3], [0.05]])
     v = np.concatenate([prob.v, [-0.01, -0.02, -0.03], [prob.v[0]]])
-    off = np.concatenate([prob.batch_off, [prob.n_pts + 3, prob.n_pts + 4]]).astype(np.int64)
+    off = np.concatenate([[0], prob.batch_off, [prob.n_pts + 3, prob.n_pts + 3, prob.n_pts + 4]]).astype(np.int64)
     edge = W.Problem("water-edge", prob.radials, prob.species, prob.atom_off, prob.atom_species, prob.atom_xyz,
                      pts, w, off, np.zeros(len(off) - 1, dtype=np.int32), v)
     Href = O.h_matrix(B, pts, w, v)
