@@ -79,7 +79,8 @@ class ClockSampler:
 
     def __init__(self, index):
         self.index = index
-        self.lines = []
+        self.lines = []              # (host monotonic time, csv line)
+        self.window = None           # (start, end) of the timed region
         self.proc = None
 
     def __enter__(self):
@@ -90,13 +91,22 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # wait (3 s at most) for the first sample, so that sampling is
+            # running through the whole timed region that follows
+            t0 = time.monotonic()
+            while not self.lines and self.proc.poll() is None and time.monotonic() - t0 < 3.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, start, end):
+        """Keep only the samples taken while [start, end] ran (host clock)."""
+        self.window = (start, end)
 
     def __exit__(self, *a):
         if self.proc:
@@ -109,7 +119,12 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = self.lines
+        if self.window is not None:
+            # a sample line arrives up to one interval after it was taken
+            inside = [r for r in rows if self.window[0] <= r[0] <= self.window[1] + 0.25]
+            rows = inside if inside else rows
+        for _, ln in rows:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -258,7 +273,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="si64")
@@ -372,7 +387,9 @@ def main():
 
     ctx.profile(True) if graph is None else None
     with ClockSampler(local) as clk:
+        t_start = time.monotonic()
         times = timed(args.steps, run)
+        clk.mark(t_start, time.monotonic())
     ms = statistics.mean(times)
     prof = {}
     if graph is None:
