@@ -50,11 +50,6 @@ struct Wave {
     size_t ws_elems = 0;           // FP64 elements of the Phi block
 };
 
-template <typename T>
-struct Slot {                     // an array inside the device arena
-    size_t off = 0, n = 0;
-};
-
 // Allocator whose value-less construct leaves the element uninitialised, so
 // that resize() of a large buffer does not zero it on one thread before a
 // parallel loop fills it (the fill is then also the pages' first touch).
