@@ -5,7 +5,6 @@ results used to check the oracle from outside.
 """
 from __future__ import annotations
 
-import itertools
 import math
 
 import numpy as np

@@ -10,7 +10,6 @@ refused with a clear error.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 import torch
 
