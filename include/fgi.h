@@ -78,7 +78,9 @@ typedef enum {
 } fgi_precision;
 
 /* Create a context on CUDA device `cuda_device`.  FGI_ERR_UNSUPPORTED if the
-   device is not compute capability 10.3.  cuda_device = -1 creates a
+   device is not compute capability 10.3, FGI_ERR_CUDA if the CUDA runtime
+   finds no driver or device, FGI_ERR_ARG for an index beyond the devices
+   present.  There is no CPU fallback.  cuda_device = -1 creates a
    host-only context: inputs, plan tables, pattern and workspace queries
    work; the compute calls return FGI_ERR_STATE. */
 int fgi_create(fgi_ctx **out, int cuda_device);

@@ -866,8 +866,8 @@ int fgi_create(fgi_ctx **out, int cuda_device)
         return FGI_OK;
     }
     int n = 0;
-    if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n)
-        return FGI_ERR_ARG;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) return FGI_ERR_CUDA;   // no driver or no device
+    if (cuda_device < 0 || cuda_device >= n) return FGI_ERR_ARG;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) return FGI_ERR_CUDA;
     if (!(prop.major == 10 && prop.minor == 3)) return FGI_ERR_UNSUPPORTED;

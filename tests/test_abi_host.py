@@ -260,3 +260,18 @@ def test_batch_beyond_the_function_limit_is_refused(fgi, water):
     ctx.set_systems([0, 58], np.full(58, sp, np.int32), xyz[:58])
     ctx.plan("split_bf16")
     assert ctx.batch_work()[1][0] == 58 * 140
+
+
+def test_no_fallback_without_the_library_or_a_device(fgi, tmp_path):
+    """The compute path has no CPU fallback: a missing libfgi.so is an
+    ImportError, and without a CUDA device a device context cannot be
+    created at all (host-only contexts only plan)."""
+    from paper_2208_12335_gb300 import fgi as F
+    with pytest.raises(ImportError):
+        F.load_library(str(tmp_path / "libfgi.so"))
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(fgi.FGIError) as e:
+        fgi.Context(0)
+    assert e.value.code == -3                      # FGI_ERR_CUDA: no driver or device
