@@ -163,6 +163,7 @@ class Context:
         xyz = _np(xyz, np.float64)
         self._check(self._lib.fgi_set_systems(self._h, len(atom_off) - 1, _ptr(atom_off), _ptr(species),
                                               _ptr(xyz)))
+        self._n_sys = len(atom_off) - 1
 
     def set_grid(self, xyz, w, batch_off, batch_sys):
         xyz = _np(xyz, np.float64)
@@ -268,7 +269,7 @@ class Context:
         if n is None:
             n = torch.empty(n_pts, dtype=torch.float64, device=d.device)
         _dev_f64(n, n_pts, "n")
-        n_sys = len(self._sys_list())
+        n_sys = self.n_systems()
         if traces is None and with_traces:
             traces = torch.empty(n_sys, dtype=torch.float64, device=d.device)
         ws = self.workspace() if ws is None else ws
@@ -294,7 +295,7 @@ class Context:
         _dev_f64(a, nnz, "a")
         _dev_f64(b, nnz, "b")
         if out is None:
-            out = torch.empty(len(self._sys_list()), dtype=torch.float64, device=a.device)
+            out = torch.empty(self.n_systems(), dtype=torch.float64, device=a.device)
         self._check(self._lib.fgi_trace(self._h, _ptr(a), _ptr(b), _ptr(out), _stream(stream)))
         return out
 
@@ -316,16 +317,15 @@ class Context:
         self._check(self._lib.fgi_profile_read(self._h, k, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
         return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
-    def _sys_list(self):
-        out = []
-        s = 0
-        while True:
-            rc = self._lib.fgi_get_system(self._h, s, None, None, None, None)
-            if rc != 0:
-                break
-            out.append(s)
-            s += 1
-        return out
+    def n_systems(self) -> int:
+        """Number of systems given to set_systems."""
+        n = getattr(self, "_n_sys", None)
+        if n is None:                                   # context filled through the C ABI directly
+            n = 0
+            while self._lib.fgi_get_system(self._h, n, None, None, None, None) == 0:
+                n += 1
+            self._n_sys = n
+        return n
 
 
 class HIntegrate(torch.autograd.Function):
