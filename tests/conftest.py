@@ -8,4 +8,9 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
-    config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "slow: long-running test, collected after the others")
+
+
+def pytest_collection_modifyitems(config, items):
+    # long-running tests last, so that a quick failure elsewhere shows first
+    items.sort(key=lambda it: it.get_closest_marker("slow") is not None)

@@ -1,0 +1,88 @@
+"""GPU parity on the 1000-atom C/H/N/O cluster (geometry, species and grid
+recipe of the 1000-atom workload) through the C ABI.
+
+The grids of two of its atoms (a carbon and a hydrogen, 70 x 590 points
+each, Becke weights over all 1000 atoms) are generated, and 24 seeded
+batches of those (113-387 points, 302-1109 active functions) are
+integrated: H in FP64, split BF16 and plain BF16, and the density in FP64
+and split BF16, against the FP64 oracle on the same points.  Collected
+last (marked slow): the oracle and the generator take a few seconds.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL_FP64 = 1e-11
+TOL_SPLIT_H = 1e-7
+TOL_SPLIT_N = 1e-7
+TOL_BF16_H = 2e-2
+
+
+@pytest.fixture(scope="module")
+def fgi():
+    from paper_2208_12335_gb300 import build as B
+    B.build()
+    import paper_2208_12335_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return P
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def chno_sub():
+    full = W.chno_cluster(atoms_with_grid=[0, 1])
+    assert sorted(full.atom_species[:2].tolist()) == [0, 1]          # one H, one C
+    ids = np.sort(np.random.default_rng(5).choice(full.n_batch, size=24, replace=False))
+    prob = full.subgrid(ids)
+    B = O.system_basis(prob)
+    act = O.active_functions(B, prob.pts)
+    H = O.h_matrix(B, prob.pts, prob.w, prob.v, sub=act)
+    D, _ = W.density_matrix_occ(len(act), int(0.28 * len(act)), np.random.default_rng(1))
+    n = O.density(B, prob.pts, D, sub=act)
+    return prob, B, act, H, D, n
+
+
+def on_pattern(ctx, n_fn, act, M):
+    """Stored values of the sub-block matrix M (rows/columns = act); zero
+    where a function is not active on any point."""
+    rowptr, col = ctx.pattern(0)
+    r = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    pos = -np.ones(n_fn, dtype=np.int64)
+    pos[act] = np.arange(len(act))
+    inside = (pos[r] >= 0) & (pos[col] >= 0)
+    out = np.zeros(len(r))
+    out[inside] = M[pos[r[inside]], pos[col[inside]]]
+    return out, inside
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", None), ("split_bf16", TOL_SPLIT_H), ("bf16", TOL_BF16_H)])
+def test_h_on_the_1000_atom_cluster(fgi, chno_sub, precision, tol):
+    prob, B, act, H, _, _ = chno_sub
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    ctx.sync()
+    ref, inside = on_pattern(ctx, B.n_fn, act, H)
+    err = np.max(np.abs(h - ref))
+    bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(H).max())
+    assert np.all(h[~inside] == 0.0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split_bf16", TOL_SPLIT_N)])
+def test_density_on_the_1000_atom_cluster(fgi, chno_sub, precision, tol):
+    prob, B, act, _, D, nref = chno_sub
+    ctx = fgi.Context(0).load(prob, precision)
+    d, _ = on_pattern(ctx, B.n_fn, act, D)
+    n, _ = ctx.density(dev(d))
+    ctx.sync()
+    rel = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
+    assert rel <= tol, (precision, rel)
