@@ -13,6 +13,7 @@
 #include <utility>
 #include <vector>
 
+#include "fgi_bounds.h"
 #include "fgi_internal.h"
 #include "fgi_tc.h"
 #include "../../include/fgi.h"
@@ -211,6 +212,8 @@ void wave_work(fgi_ctx *c);
 //   wave_mb            operand-image workspace per wave, MiB
 //   h_sb_points        super-batch point limit of the H path (0: none, <= 1024)
 //   h_sb_growth        the H path's limit on the union's functions / largest member's
+//   bound_grids        1: the split images take their leading-digit grids from
+//                      table bounds of |phi| instead of a pass over the points
 // Unknown keys are ignored; a malformed value is an argument error.
 struct TuneSettings {
     int sb_points = 1024;
@@ -218,6 +221,7 @@ struct TuneSettings {
     long long wave_mb = 0;      // 0: the library default
     int h_sb_points = 400;      // merges small neighbouring batches; no deeper K than the largest batches
     double h_sb_growth = 1.25;
+    int bound_grids = 0;
 };
 
 int read_tune_file(const char *path, TuneSettings &t, std::string *err)
@@ -271,6 +275,13 @@ int read_tune_file(const char *path, TuneSettings &t, std::string *err)
                 break;
             }
             t.wave_mb = (long long)val;
+        } else if (k == "bound_grids") {
+            if (!(val == 0.0 || val == 1.0)) {
+                *err = "tune file: bound_grids must be 0 or 1";
+                rc = FGI_ERR_ARG;
+                break;
+            }
+            t.bound_grids = (int)val;
         }
     }
     fclose(f);
@@ -289,7 +300,13 @@ int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
     if (const char *e = getenv("FGI_SB_GROWTH")) ts.sb_growth = atof(e);
     if (const char *e = getenv("FGI_H_SB_POINTS")) ts.h_sb_points = atoi(e);
     if (const char *e = getenv("FGI_H_SB_GROWTH")) ts.h_sb_growth = atof(e);
+    if (const char *e = getenv("FGI_BOUND_GRIDS")) ts.bound_grids = atoi(e) != 0;
     tin.wave_mb = ts.wave_mb;
+    tin.pts = c->pts.data();
+    // the table bounds need u(0) = 0 for every radial (u(r)/r bounded at 0)
+    bool bounded = true;
+    for (const RadialH &r : c->radials) bounded = bounded && !r.coef.empty() && r.coef[0] == 0.0;
+    tin.bound_grids = ts.bound_grids && bounded ? 1 : 0;
     tin.sb_points = ts.h_sb_points;
     tin.sb_growth = ts.h_sb_growth;
     int rc = tc_build(c->tc, tin, err);
@@ -525,8 +542,18 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         d.inv_h_lo = (float)(d.inv_h - (double)d.inv_h_hi);
         d.rcut_f = (float)d.rcut;
         d.pad = 0;
+        d.bound_off = 0;
         coef.insert(coef.end(), r.coef.begin(), r.coef.end());
         drad.push_back(d);
+    }
+    // bounds of |phi|: max |Y_lm|, then per radial the suffix bounds of |u(r)/r|
+    std::vector<float> rbound(kYlmMaxEntries);
+    ylm_abs_max(rbound.data());
+    for (size_t i = 0; i < c->radials.size(); i++) {
+        const RadialH &r = c->radials[i];
+        drad[i].bound_off = (long long)rbound.size();
+        rbound.resize(rbound.size() + (size_t)(r.nk - 1));
+        radial_over_r_bounds(r.coef.data(), r.nk - 1, r.h, rbound.data() + drad[i].bound_off);
     }
     // coefficients as double-floats: per interval (hi0..hi3), (lo0..lo3)
     std::vector<float> coef_dd(coef.size() * 2);
@@ -643,7 +670,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_items = add(c->items.data(), c->items.size() * sizeof(WorkItem)),
            i_sv0 = add(sys_val0.data(), sys_val0.size() * 8), i_sf0 = add(sys_fn0.data(), sys_fn0.size() * 8),
            i_fsys = add(c->fn_sys.data(), c->fn_sys.size() * 4), i_status = add(nullptr, 64),
-           i_snnz = add(sys_nnz.data(), sys_nnz.size() * 8), i_colg = add(col_glob.data(), col_glob.size() * 4);
+           i_snnz = add(sys_nnz.data(), sys_nnz.size() * 8), i_colg = add(col_glob.data(), col_glob.size() * 4),
+           i_rbnd = add(rbound.data(), rbound.size() * 4);
     cudaError_t e = cudaMalloc((void **)&c->d_arena, total);
     if (e != cudaSuccess) {
         c->d_arena = nullptr;
@@ -686,6 +714,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     c->d_fn_sys = (int *)at(i_fsys);
     c->d_sys_nnz = (long long *)at(i_snnz);
     P.col_glob = (const int *)at(i_colg);
+    P.rbound = (const float *)at(i_rbnd);
     c->d_status = (int *)at(i_status);
 
     // tensor-core path plan (operand images, tiles, waves)

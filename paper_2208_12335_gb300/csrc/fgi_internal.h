@@ -23,6 +23,7 @@ struct DevRadial {
     float inv_h_hi, inv_h_lo;   // 1/h as a double-float
     float rcut_f;               // cutoff rounded to FP32
     int pad;
+    long long bound_off;        // first entry of its suffix bounds of |u(r)/r| in DevPlan::rbound
 };
 
 struct DevSpecies {
@@ -85,6 +86,10 @@ struct DevPlan {
     const DevBatch *batches;
     const DevAct *act;
     int *status;
+    // bounds of |phi| (leading-digit grids without a pass over the points):
+    // [16] max |Y_lm| (index l*l + l + m), then per radial, per knot
+    // interval k, a bound of |u(r)/r| over r >= k h
+    const float *rbound;
 };
 
 // ---- launchers (return the launch status) ----

@@ -28,6 +28,7 @@ struct TcBatch {
     int nc_alloc;          // allocated 64-point chunks (even)
     int nkc;               // 64-function chunks (density contraction depth)
     long long part0;       // first partial-density row of the batch in its wave (128 doubles each)
+    float cen[3], rad;     // a sphere holding the batch's points (rounded outward)
 };
 
 struct TcWave {
@@ -55,6 +56,8 @@ struct TcPlanInput {
     long long n_fn = 0;                  // functions (all systems)
     bool host_only = false;              // build host tables only (no device copies)
     long long wave_mb = 0;               // operand images per wave, MiB (0: default)
+    const double *pts = nullptr;         // [n_pts][3] points (bounding spheres of the batches)
+    int bound_grids = 0;                 // leading-digit grids from table bounds, no pass over the points
 };
 
 struct TcPlan {
@@ -66,6 +69,7 @@ struct TcPlan {
     size_t sign_off = 0;                 // workspace offset of the per-batch sign of w v (H images)
     long long nnz = 0, n_fn = 0;
     int num_sms = 1;                     // persistent grids: one CTA per SM
+    int bound_grids = 0;                 // see TcPlanInput
     std::vector<DevBatch> sb;            // super-batches (points, union of active atoms)
     std::vector<DevAct> sact;            // their active-atom entries
     std::vector<int> sb_first;           // first input batch of each super-batch (+ n_batch at the end)

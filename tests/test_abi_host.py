@@ -216,8 +216,12 @@ def test_tune_file_is_read_and_checked(fgi, water, tmp_path):
         ctx.plan("split_bf16", str(bad))
     assert e.value.code == -1
     ok = tmp_path / "ok.txt"
-    ok.write_text("h_sb_points 256\nh_sb_growth 1.2\n")
+    ok.write_text("h_sb_points 256\nh_sb_growth 1.2\nbound_grids 1\n")
     ctx.plan("split_bf16", str(ok))
+    bad.write_text("bound_grids 2\n")
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.plan("split_bf16", str(bad))
+    assert e.value.code == -1
     bad.write_text("density_sb_growth\n")
     with pytest.raises(fgi.FGIError) as e:
         ctx.plan("split_bf16", str(bad))
