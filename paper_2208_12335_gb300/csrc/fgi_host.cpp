@@ -212,8 +212,9 @@ void wave_work(fgi_ctx *c);
 //   wave_mb            operand-image workspace per wave, MiB
 //   h_sb_points        super-batch point limit of the H path (0: none, <= 1024)
 //   h_sb_growth        the H path's limit on the union's functions / largest member's
-//   bound_grids        1: the split images take their leading-digit grids from
-//                      table bounds of |phi| instead of a pass over the points
+//   bound_grids        leading-digit grids of the split images from table
+//                      bounds of |phi| instead of a pass over the points:
+//                      0 none, 1 the density images, 2 also the H images
 // Unknown keys are ignored; a malformed value is an argument error.
 struct TuneSettings {
     int sb_points = 1024;
@@ -276,8 +277,8 @@ int read_tune_file(const char *path, TuneSettings &t, std::string *err)
             }
             t.wave_mb = (long long)val;
         } else if (k == "bound_grids") {
-            if (!(val == 0.0 || val == 1.0)) {
-                *err = "tune file: bound_grids must be 0 or 1";
+            if (!(val == 0.0 || val == 1.0 || val == 2.0)) {
+                *err = "tune file: bound_grids must be 0, 1 or 2";
                 rc = FGI_ERR_ARG;
                 break;
             }
@@ -300,13 +301,13 @@ int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
     if (const char *e = getenv("FGI_SB_GROWTH")) ts.sb_growth = atof(e);
     if (const char *e = getenv("FGI_H_SB_POINTS")) ts.h_sb_points = atoi(e);
     if (const char *e = getenv("FGI_H_SB_GROWTH")) ts.h_sb_growth = atof(e);
-    if (const char *e = getenv("FGI_BOUND_GRIDS")) ts.bound_grids = atoi(e) != 0;
+    if (const char *e = getenv("FGI_BOUND_GRIDS")) ts.bound_grids = std::min(std::max(atoi(e), 0), 2);
     tin.wave_mb = ts.wave_mb;
     tin.pts = c->pts.data();
     // the table bounds need u(0) = 0 for every radial (u(r)/r bounded at 0)
     bool bounded = true;
     for (const RadialH &r : c->radials) bounded = bounded && !r.coef.empty() && r.coef[0] == 0.0;
-    tin.bound_grids = ts.bound_grids && bounded ? 1 : 0;
+    tin.bound_grids = bounded ? ts.bound_grids : 0;
     tin.sb_points = ts.h_sb_points;
     tin.sb_growth = ts.h_sb_growth;
     int rc = tc_build(c->tc, tin, err);

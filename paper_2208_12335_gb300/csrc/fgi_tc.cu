@@ -1923,7 +1923,7 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
                                                        (uint8_t *)ws + t.img_base, v, n_split, fixed,
                                                        reinterpret_cast<int *>((uint8_t *)ws + t.sign_off),
-                                                       t.bound_grids);
+                                                       t.bound_grids >= 2 ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1932,7 +1932,8 @@ cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &
 {
     if (w.npc <= 0) return cudaSuccess;
     k_tc_phi_cols<<<(unsigned)w.npc, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0,
-                                                           (uint8_t *)ws + t.img_base, n_split, t.bound_grids);
+                                                           (uint8_t *)ws + t.img_base, n_split,
+                                                           t.bound_grids >= 1 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ struct TcPlanInput {
     bool host_only = false;              // build host tables only (no device copies)
     long long wave_mb = 0;               // operand images per wave, MiB (0: default)
     const double *pts = nullptr;         // [n_pts][3] points (bounding spheres of the batches)
-    int bound_grids = 0;                 // leading-digit grids from table bounds, no pass over the points
+    int bound_grids = 0;                 // leading-digit grids from table bounds: 1 density, 2 also H
 };
 
 struct TcPlan {

@@ -218,7 +218,7 @@ def test_tune_file_is_read_and_checked(fgi, water, tmp_path):
     ok = tmp_path / "ok.txt"
     ok.write_text("h_sb_points 256\nh_sb_growth 1.2\nbound_grids 1\n")
     ctx.plan("split_bf16", str(ok))
-    bad.write_text("bound_grids 2\n")
+    bad.write_text("bound_grids 3\n")
     with pytest.raises(fgi.FGIError) as e:
         ctx.plan("split_bf16", str(bad))
     assert e.value.code == -1

@@ -1,8 +1,11 @@
 """GPU parity of the split path with leading-digit grids taken from table
-bounds of |phi| (tune-file key bound_grids 1) instead of a pass over the
-points: H and density against the FP64 oracle on water, a Si64 sub-grid and
-a sample of the 1000-atom C/H/N/O cluster, at the split tolerances.
-Marked slow (collected last)."""
+bounds of |phi| instead of a pass over the points (tune-file key
+bound_grids: 1 the density images, 2 the H images too): H and density
+against the FP64 oracle on water, a Si64 sub-grid and a sample of the
+1000-atom C/H/N/O cluster, at the split tolerances.  Marked slow
+(collected last)."""
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -30,6 +33,7 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
 
 
+@functools.lru_cache(maxsize=None)
 def problem(name):
     if name == "water":
         return W.tiny_water()
@@ -53,8 +57,9 @@ def on_pattern(ctx, n_fn, act, M):
     return out
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["water", "si64", "chno"])
-def test_table_bound_grids_keep_split_parity(fgi, tmp_path, name):
+def test_table_bound_grids_keep_split_parity(fgi, tmp_path, name, mode):
     prob = problem(name)
     B = O.system_basis(prob)
     act = O.active_functions(B, prob.pts)
@@ -62,12 +67,12 @@ def test_table_bound_grids_keep_split_parity(fgi, tmp_path, name):
     D, _ = W.density_matrix_occ(len(act), max(1, int(0.28 * len(act))), np.random.default_rng(1))
     nref = O.density(B, prob.pts, D, sub=act)
     settings = tmp_path / "bound.txt"
-    settings.write_text("bound_grids 1\n")
+    settings.write_text("bound_grids %d\n" % mode)
     ctx = fgi.Context(0).load(prob, "split_bf16", tune_path=str(settings))
     h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
     n, _ = ctx.density(dev(on_pattern(ctx, B.n_fn, act, D)))
     ctx.sync()
     err_h = np.max(np.abs(h - on_pattern(ctx, B.n_fn, act, H)))
     rel_n = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
-    assert err_h <= TOL_SPLIT_H, (name, err_h)
-    assert rel_n <= TOL_SPLIT_N, (name, rel_n)
+    assert err_h <= TOL_SPLIT_H, (name, mode, err_h)
+    assert rel_n <= TOL_SPLIT_N, (name, mode, rel_n)
