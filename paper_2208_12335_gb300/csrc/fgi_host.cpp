@@ -303,7 +303,6 @@ int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
     if (const char *e = getenv("FGI_H_SB_GROWTH")) ts.h_sb_growth = atof(e);
     if (const char *e = getenv("FGI_BOUND_GRIDS")) ts.bound_grids = std::min(std::max(atoi(e), 0), 2);
     tin.wave_mb = ts.wave_mb;
-    tin.pts = c->pts.data();
     // the table bounds need u(0) = 0 for every radial (u(r)/r bounded at 0)
     bool bounded = true;
     for (const RadialH &r : c->radials) bounded = bounded && !r.coef.empty() && r.coef[0] == 0.0;

@@ -529,41 +529,6 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 
 constexpr int kPhiThreads = 256;
 
-// Bound of |phi_j(p)| over every point p of the batch for local function j,
-// from the plan's tables: the suffix bound of |u(r)/r| at a lower bound of
-// the distance from the atom to the batch's sphere, times max |Y_lm|.  The
-// distance is shortened against FP32 rounding and the knot index taken from
-// below, so the bound holds; zero when the whole sphere is beyond the shell's
-// cutoff.
-__device__ __forceinline__ float row_bound(const DevPlan &P, const DevAct *act, int n_act, const TcBatch &T, int j)
-{
-    const DevAct A = act[find_act(act, n_act, j)];
-    const DevSpecies S = P.species[P.atom_species[A.atom]];
-    int f = j - A.fn_loc;
-    for (int sh = 0; sh < S.n_shell; sh++) {
-        const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
-        const int nm = 2 * R.l + 1;
-        if (f < nm) {
-            const float *aa = P.atom_dd + 6 * A.atom;
-            const float dx = (aa[0] + aa[1]) - T.cen[0];
-            const float dy = (aa[2] + aa[3]) - T.cen[1];
-            const float dz = (aa[4] + aa[5]) - T.cen[2];
-            const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
-            // FP32 rounding of the coordinates (relative 2^-24 of their size)
-            // and of the distance: 1e-5 (1 + d) + 4e-6 |cen|_1 covers both
-            const float slack = 1e-5f * (dc + 1.f) + 4e-6f * (fabsf(T.cen[0]) + fabsf(T.cen[1]) + fabsf(T.cen[2]));
-            const float dmin = dc - T.rad - slack;
-            if (dmin >= R.rcut_f) return 0.f;
-            int k = dmin > 0.f ? (int)(dmin * R.inv_h_hi * 0.999999f) : 0;
-            k = min(k, R.nk - 2);
-            const float b = __ldg(P.rbound + R.bound_off + k) * __ldg(P.rbound + R.l * R.l + f);
-            return fminf(b, 1.0e30f);
-        }
-        f -= nm;
-    }
-    return 0.f;
-}
-
 __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed,
                                                 int *bsign, int bound)
@@ -574,7 +539,6 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
     __shared__ float rowsum[2][128];                 // sums of |phi|, |w v phi| over the points
     __shared__ float fsc[2][128][2];                 // per row: scale, unit
     __shared__ float wvf[kMaxBatchPoints];           // |w v| per point (FP32), first pass
-    __shared__ unsigned int wv_max;                  // max |w v| over the batch (float bits), table bounds
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
     const TcBatch T = tb[it.batch];
@@ -591,35 +555,72 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
     // single image psi = phi sqrt|w v| for both operands, H = s psi^T psi;
     // mixed signs keep the phi and w v phi images
     bool pos = false, neg = false;
-    const bool tab = fixed && bound;
-    if (tab) {
-        if (threadIdx.x == 0) wv_max = 0u;
-        __syncthreads();
-    }
-    float wmx = 0.f;
     for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
         const double wv = P.pw[B.pt0 + p] * v[B.pt0 + p];
         pos |= wv > 0.0;
         neg |= wv < 0.0;
-        wmx = fmaxf(wmx, (float)fabs(wv));
     }
-    if (tab && wmx > 0.f) atomicMax(&wv_max, __float_as_uint(fminf(wmx, 1.0e30f)));
     pos = __syncthreads_or(pos) != 0;
     neg = __syncthreads_or(neg) != 0;
     const int sgn = (pos && neg) ? 0 : (neg ? -1 : 1);
     if (I == 0 && threadIdx.x == 0) bsign[it.batch] = sgn;
-    if (tab) {
-        // row bounds from the tables instead of a pass over the points; the
-        // row sums are unknown, so the digit width follows the depth alone
-        const float wm = __uint_as_float(wv_max) * (1.f + 1.f / 1048576.f);
-        const float wfac = sgn != 0 ? sqrtf(wm) * (1.f + 1.f / 1048576.f) : wm;
-        for (int r = threadIdx.x; r < 128; r += blockDim.x) {
-            const int j = r0 + r;
-            const float b = j < B.nfn ? row_bound(P, act, B.n_act, T, j) : 0.f;
-            rowmax[0][r] = __float_as_uint(b);
-            rowmax[1][r] = __float_as_uint(fminf(b * wfac, 1.0e30f));
-            rowsum[0][r] = 1.0e30f;
-            rowsum[1][r] = 1.0e30f;
+    if (fixed && bound) {
+        // row bounds from the tables: per (atom, shell) job and point one
+        // lookup of the suffix bound of |u(r)/r| at the point's distance
+        // (double-float differences, knot index taken from below), times
+        // sqrt|w v| (psi) or |w v| (w v phi) of the point; then max |Y_lm|
+        // per row.  No row sums: the digit width follows the depth alone.
+        for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+            (&rowmax[0][0])[q] = 0u;          // rows past n_b stay zero
+            (&rowsum[0][0])[q] = 1.0e30f;
+        }
+        for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
+            const float a = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p])) * (1.f + 1.f / 1048576.f);
+            wvf[p] = fminf(sgn != 0 ? sqrtf(a) * (1.f + 1.f / 1048576.f) : a, 1.0e30f);
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+        int job = 0;
+        for (int e = e0; e <= e1; e++) {
+            const DevAct A = act[e];
+            const DevSpecies S = P.species[P.atom_species[A.atom]];
+            const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
+            const float *aa = P.atom_dd + 6 * A.atom;
+            int f = 0;
+            for (int sh = 0; sh < S.n_shell; sh++) {
+                const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                const int nm = 2 * R.l + 1;
+                const int f1 = f;
+                f += nm;
+                if (f <= f_lo || f1 >= f_hi) continue;
+                if ((job++ % nwarp) != warp) continue;
+                const float *tabr = P.rbound + R.bound_off;
+                float m0 = 0.f, m1 = 0.f;
+                for (int p = lane; p < B.np; p += 32) {
+                    const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                    const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+                    const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+                    const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+                    const float d = sqrtf(x * x + y * y + z * z);
+                    if (d >= R.rcut_f * 1.00001f) continue;
+                    const int ki = min(max((int)(d * 0.999999f * R.inv_h_hi), 0), R.nk - 2);
+                    const float t = __ldg(tabr + ki);
+                    m0 = fmaxf(m0, t);
+                    m1 = fmaxf(m1, t * wvf[p]);
+                }
+                m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
+                m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
+                if (lane == 0) {
+                    for (int m = 0; m < nm; m++) {
+                        const int fr = f1 + m;
+                        if (fr < f_lo || fr >= f_hi) continue;
+                        const int row = A.fn_loc + fr - r0;
+                        const float yl = __ldg(P.rbound + R.l * R.l + m);
+                        rowmax[0][row] = __float_as_uint(fminf(m0 * yl, 1.0e30f));
+                        rowmax[1][row] = __float_as_uint(fminf(m1 * yl, 1.0e30f));
+                    }
+                }
+            }
         }
         __syncthreads();
         for (int q = threadIdx.x; q < 256; q += blockDim.x) {
@@ -1735,33 +1736,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         T.plane_d = (long long)T.nrb * T.nkc * kChunkBytes;
         foot[b] = 3 * (size_t)T.plane_phi + 3 * (size_t)std::max(T.plane_phi, T.plane_d);
     }
-    // a sphere around each super-batch's points: the centre of the bounding
-    // box and the largest distance to it, rounded outward in FP32
     t.bound_grids = in.bound_grids;
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int b = 0; b < n_sb; b++) {
-        const DevBatch &B = t.sb[b];
-        TcBatch &T = t.batches[b];
-        T.cen[0] = T.cen[1] = T.cen[2] = 0.f;
-        T.rad = 0.f;
-        if (!in.pts || B.np <= 0) continue;
-        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-        for (long long p = B.pt0; p < B.pt0 + B.np; p++)
-            for (int k = 0; k < 3; k++) {
-                lo[k] = std::min(lo[k], in.pts[3 * p + k]);
-                hi[k] = std::max(hi[k], in.pts[3 * p + k]);
-            }
-        float cen[3];
-        for (int k = 0; k < 3; k++) cen[k] = (float)(0.5 * (lo[k] + hi[k]));
-        double r2 = 0.0;
-        for (long long p = B.pt0; p < B.pt0 + B.np; p++) {
-            double d2 = 0.0;
-            for (int k = 0; k < 3; k++) d2 += (in.pts[3 * p + k] - cen[k]) * (in.pts[3 * p + k] - cen[k]);
-            r2 = std::max(r2, d2);
-        }
-        for (int k = 0; k < 3; k++) T.cen[k] = cen[k];
-        T.rad = (float)(std::sqrt(r2) * (1.0 + 1e-6) + 1e-6);
-    }
     size_t max_ws = 0;
     TcWave w;
     size_t off = 0;

@@ -28,7 +28,6 @@ struct TcBatch {
     int nc_alloc;          // allocated 64-point chunks (even)
     int nkc;               // 64-function chunks (density contraction depth)
     long long part0;       // first partial-density row of the batch in its wave (128 doubles each)
-    float cen[3], rad;     // a sphere holding the batch's points (rounded outward)
 };
 
 struct TcWave {
@@ -56,7 +55,6 @@ struct TcPlanInput {
     long long n_fn = 0;                  // functions (all systems)
     bool host_only = false;              // build host tables only (no device copies)
     long long wave_mb = 0;               // operand images per wave, MiB (0: default)
-    const double *pts = nullptr;         // [n_pts][3] points (bounding spheres of the batches)
     int bound_grids = 0;                 // leading-digit grids from table bounds: 1 density, 2 also H
 };
 
