@@ -279,3 +279,15 @@ def test_no_fallback_without_the_library_or_a_device(fgi, tmp_path):
     with pytest.raises(fgi.FGIError) as e:
         fgi.Context(0)
     assert e.value.code == -3                      # FGI_ERR_CUDA: no driver or device
+
+
+def test_every_autotuner_candidate_plans(fgi, water, tmp_path):
+    """The autotuner's default candidates are settings the planner accepts."""
+    from paper_2208_12335_gb300 import tune as T
+    for i, cand in enumerate(T.DEFAULT_CANDIDATES):
+        path = tmp_path / ("cand%d.txt" % i)
+        T.write_settings(str(path), cand)
+        assert T.read_settings(str(path)) == {k: float(v) for k, v in cand.items()}
+        ctx = host_ctx(fgi, water)
+        ctx.plan("split_bf16", str(path))
+        assert ctx.workspace_size() > 0
