@@ -9,6 +9,7 @@
 #pragma once
 #include <cmath>
 #include <limits>
+#include <utility>
 
 namespace fgi {
 
@@ -43,29 +44,86 @@ inline void ylm_abs_max(float out[kYlmMaxEntries])
     for (int i = 0; i < kYlmMaxEntries; i++) out[i] = (float)(v[i] * (1.0 + 1.0 / 1024.0));
 }
 
-// max |c0 + c1 t + c2 t^2 + c3 t^3| over t in [0, 1]: the end points and the
-// stationary points inside the interval.
-inline double cubic_abs_max(const double *cf)
+// Roots in (0, 1) of the quadratic a t^2 + b t + c, ascending; returns the count.
+inline int quadratic_roots01(double a, double b, double c, double *r)
 {
-    auto u = [&](double t) { return cf[0] + t * (cf[1] + t * (cf[2] + t * cf[3])); };
-    double m = std::fmax(std::fabs(u(0.0)), std::fabs(u(1.0)));
-    // u'(t) = c1 + 2 c2 t + 3 c3 t^2
-    const double A = 3.0 * cf[3], B = 2.0 * cf[2], C = cf[1];
-    double roots[2];
-    int nr = 0;
-    if (A == 0.0) {
-        if (B != 0.0) roots[nr++] = -C / B;
+    int n = 0;
+    double t[2];
+    if (a == 0.0) {
+        if (b != 0.0) t[n++] = -c / b;
     } else {
-        const double disc = B * B - 4.0 * A * C;
+        const double disc = b * b - 4.0 * a * c;
         if (disc >= 0.0) {
             const double sq = std::sqrt(disc);
-            const double qq = -0.5 * (B + (B >= 0.0 ? sq : -sq));
-            roots[nr++] = qq / A;
-            if (qq != 0.0) roots[nr++] = C / qq;
+            const double q = -0.5 * (b + (b >= 0.0 ? sq : -sq));
+            if (q != 0.0) {
+                t[n++] = q / a;
+                t[n++] = c / q;
+            } else {
+                t[n++] = 0.0;   // b = 0 and c = 0: the double root t = 0
+            }
         }
     }
-    for (int i = 0; i < nr; i++)
-        if (roots[i] > 0.0 && roots[i] < 1.0) m = std::fmax(m, std::fabs(u(roots[i])));
+    int m = 0;
+    for (int i = 0; i < n; i++)
+        if (t[i] > 0.0 && t[i] < 1.0) r[m++] = t[i];
+    if (m == 2 && r[0] > r[1]) std::swap(r[0], r[1]);
+    return m;
+}
+
+// max |u(r)/r| over knot interval j of a radial spline with coefficients cf
+// (u = c0 + t (c1 + t (c2 + t c3)), r = h (j + t), t in [0, 1]).
+// j >= 1: g(t) = u/(h (j + t)) is stationary where
+//   N(t) = 2 c3 t^3 + (3 j c3 + c2) t^2 + 2 j c2 t + (j c1 - c0) = 0;
+// the roots of N' = 6 c3 t^2 + 2 (3 j c3 + c2) t + 2 j c2 cut [0, 1] into
+// pieces on which N is monotone, and each sign change is bisected to double
+// precision; the maximum is at an end point or one of those roots.
+// j = 0 (u(0) = c0 = 0): u/r = (c1 + c2 t + c3 t^2)/h, a quadratic: end
+// points and vertex.  u(0) != 0 makes u/r unbounded: +infinity.
+inline double interval_ratio_max(const double *cf, int j, double h)
+{
+    if (j == 0) {
+        if (cf[0] != 0.0) return std::numeric_limits<double>::infinity();
+        auto q = [&](double t) { return std::fabs(cf[1] + t * (cf[2] + t * cf[3])) / h; };
+        double m = std::fmax(q(0.0), q(1.0));
+        if (cf[3] != 0.0) {
+            const double tv = -cf[2] / (2.0 * cf[3]);
+            if (tv > 0.0 && tv < 1.0) m = std::fmax(m, q(tv));
+        }
+        return m;
+    }
+    const double jj = (double)j;
+    auto g = [&](double t) { return std::fabs(cf[0] + t * (cf[1] + t * (cf[2] + t * cf[3]))) / (h * (jj + t)); };
+    auto N = [&](double t) {
+        return ((2.0 * cf[3] * t + (3.0 * jj * cf[3] + cf[2])) * t + 2.0 * jj * cf[2]) * t + (jj * cf[1] - cf[0]);
+    };
+    double cuts[4];
+    int nc = 0;
+    cuts[nc++] = 0.0;
+    double r[2];
+    const int nr = quadratic_roots01(6.0 * cf[3], 2.0 * (3.0 * jj * cf[3] + cf[2]), 2.0 * jj * cf[2], r);
+    for (int i = 0; i < nr; i++) cuts[nc++] = r[i];
+    cuts[nc++] = 1.0;
+    double m = std::fmax(g(0.0), g(1.0));
+    for (int i = 0; i + 1 < nc; i++) {
+        double a = cuts[i], b = cuts[i + 1];
+        double fa = N(a), fb = N(b);
+        if (fa == 0.0) m = std::fmax(m, g(a));
+        if (fb == 0.0) m = std::fmax(m, g(b));
+        if ((fa < 0.0) == (fb < 0.0)) continue;
+        for (int it = 0; it < 100 && b - a > 0.0; it++) {
+            const double c = 0.5 * (a + b);
+            if (c <= a || c >= b) break;
+            const double fc = N(c);
+            if ((fc < 0.0) == (fa < 0.0)) {
+                a = c;
+                fa = fc;
+            } else {
+                b = c;
+            }
+        }
+        m = std::fmax(m, std::fmax(g(a), g(b)));
+    }
     return m;
 }
 
@@ -78,26 +136,15 @@ inline float round_up_float(double x)
 }
 
 // out[k] >= max |u(r)/r| over r >= k h, for k = 0 .. n_int-1, non-increasing
-// in k (beyond the last knot u = 0).  Interval j >= 1: max |u| / (j h) (r >= j h
-// there).  Interval 0: u(r)/r = (c1 + c2 t + c3 t^2)/h when c0 = u(0) = 0, so
-// (|c1| + |c2| + |c3|)/h; when u(0) != 0 the ratio is unbounded near r = 0 and
-// the entry is +infinity (the caller then keeps the pass over the points).
-// A magnitude of 1e-15 and more on |u| in an interval is rounded up by 1e-12
-// relative against the rounding of the cubic's evaluation.
+// in k (beyond the last knot u = 0): the suffix maxima of the exact
+// per-interval maxima, times (1 + 1e-12) against rounding, rounded up to
+// FP32.  Entry 0 is +infinity when u(0) != 0 (the caller then keeps the
+// pass over the points).
 inline void radial_over_r_bounds(const double *coef, int n_int, double h, float *out)
 {
     double run = 0.0;
     for (int j = n_int - 1; j >= 0; j--) {
-        const double *cf = coef + 4 * j;
-        double b;
-        if (j > 0) {
-            b = cubic_abs_max(cf) / (j * h);
-        } else if (cf[0] == 0.0) {
-            b = (std::fabs(cf[1]) + std::fabs(cf[2]) + std::fabs(cf[3])) / h;
-        } else {
-            b = std::numeric_limits<double>::infinity();
-        }
-        run = std::fmax(run, b * (1.0 + 1e-12));
+        run = std::fmax(run, interval_ratio_max(coef + 4 * j, j, h) * (1.0 + 1e-12));
         out[j] = std::isinf(run) ? std::numeric_limits<float>::infinity() : round_up_float(run);
     }
 }
