@@ -1,0 +1,122 @@
+"""The split-BF16 scheme on a CPU model of its arithmetic (tests/split_model.py)
+with exact basis values from the oracle, on 8 seeded batches of the
+1000-atom C/H/N/O cluster (CPU).
+
+What it pins: the scheme the kernels implement meets the tolerances with
+room to spare (H within 1e-8 Ha, density relative L2 within 6e-8 here),
+the two order-3 products matter (dropping them costs accuracy), and the
+leading-digit grids taken from the plan's table bounds of |phi| (the
+bound_grids setting: per point one lookup per atom shell of the suffix
+bound of |u(r)/r|, times max |Y_lm|) cost at most a few times the H error
+and nothing measurable on the density.  The tables come from
+paper_2208_12335_gb300/csrc/fgi_bounds.h through a small C++ driver."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests import split_model as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tables(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path_factory.mktemp("model") / "bounds_check")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2208_12335_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "bounds_check.cpp"), "-o", exe],
+                   check=True, capture_output=True, text=True)
+
+    def radial(r):
+        txt = "%d %.17g\n" % (len(r.coef), r.h) + "\n".join("%.17g" % c for c in np.ravel(r.coef))
+        out = subprocess.run([exe, "radial"], input=txt, capture_output=True, text=True, check=True)
+        return np.array([float(x) for x in out.stdout.split()])
+
+    out = subprocess.run([exe, "ylm"], capture_output=True, text=True, check=True)
+    return radial, np.array([float(x) for x in out.stdout.split()])
+
+
+@pytest.fixture(scope="module")
+def results(tables):
+    radial_tab, ylm = tables
+    full = W.chno_cluster(atoms_with_grid=[0, 1])
+    ids = np.sort(np.random.default_rng(11).choice(full.n_batch, size=8, replace=False))
+    prob = full.subgrid(ids)
+    B = O.system_basis(prob)
+    act_all = O.active_functions(B, prob.pts)
+    pos = -np.ones(B.n_fn, np.int64)
+    pos[act_all] = np.arange(len(act_all))
+    tabs = {rid: radial_tab(r) for rid, r in enumerate(prob.radials)}
+    Dsub, _ = W.density_matrix_occ(len(act_all), int(0.28 * len(act_all)), np.random.default_rng(1))
+    dmx, dsm = np.abs(Dsub).max(axis=1), np.abs(Dsub).sum(axis=1)
+    n = len(act_all)
+    H = {k: np.zeros((n, n)) for k in ("exact", "cur", "bound", "six")}
+    dens = {k: [] for k in ("exact", "cur", "bound")}
+    for b in range(prob.n_batch):
+        s0, s1 = prob.batch_off[b], prob.batch_off[b + 1]
+        p = prob.pts[s0:s1]
+        wv = prob.w[s0:s1] * prob.v[s0:s1]
+        assert np.all(wv <= 0)                              # one sign: H = -psi^T psi
+        act = O.active_functions(B, p)
+        phi = O.phi(B, p, sub=act)                          # points x functions
+        psi = phi * np.sqrt(np.abs(wv))[:, None]
+        depth = (len(p) + 63) // 64 * 64
+        cur = M.grid_units(np.abs(psi).max(axis=0), np.abs(psi).sum(axis=0), depth)
+        # per-point table bounds of each row, times sqrt|w v| of the point
+        bnd = np.zeros(len(act))
+        for j, i in enumerate(act):
+            r = prob.radials[B.fn_rad[i]]
+            d = np.linalg.norm(p - B.atom_xyz[B.fn_atom[i]], axis=1)
+            t = M.table_lookup(tabs[B.fn_rad[i]], r.h, r.n_knots, d) * np.sqrt(np.abs(wv))
+            bnd[j] = t.max() * ylm[r.l * r.l + r.l + B.fn_m[i]]
+        ix = np.ix_(pos[act], pos[act])
+        H["exact"][ix] -= psi.T @ psi
+        H["cur"][ix] -= M.h_block(psi, cur)
+        H["bound"][ix] -= M.h_block(psi, M.grid_units(bnd, None, depth))
+        H["six"][ix] -= M.h_block(psi, cur, n_products=6)
+        # density: D rows on global grids, points on per-point grids
+        Phi = phi.T
+        Db = Dsub[ix]
+        kdep = (len(act) + 63) // 64 * 64
+        dunit = M.grid_units(dmx[pos[act]], dsm[pos[act]], kdep)
+        pcur = M.grid_units(np.abs(Phi).max(axis=0), np.abs(Phi).sum(axis=0), kdep)
+        pmx, psm = np.zeros(len(p)), np.zeros(len(p))
+        for a in np.unique(B.fn_atom[act]):
+            d = np.linalg.norm(p - B.atom_xyz[a], axis=1)
+            for rid in np.unique(B.fn_rad[B.fn_atom == a]):
+                r = prob.radials[rid]
+                val = M.table_lookup(tabs[rid], r.h, r.n_knots, d) * ylm[r.l * r.l:r.l * r.l + 2 * r.l + 1].max()
+                pmx = np.maximum(pmx, val)
+                psm += (2 * r.l + 1) * val
+        dens["exact"].append(np.einsum("jp,jp->p", Db @ Phi, Phi))
+        dens["cur"].append(np.einsum("jp,jp->p", M.density_e(Db, dunit, Phi, pcur), Phi))
+        dens["bound"].append(np.einsum("jp,jp->p", M.density_e(Db, dunit, Phi, M.grid_units(pmx, psm, kdep)),
+                                       Phi))
+    err = {k: np.abs(H[k] - H["exact"]).max() for k in ("cur", "bound", "six")}
+    nx = np.concatenate(dens["exact"])
+    rel = {k: np.linalg.norm(np.concatenate(dens[k]) - nx) / np.linalg.norm(nx) for k in ("cur", "bound")}
+    return err, rel
+
+
+def test_split_scheme_meets_the_tolerances_with_room(results):
+    err, rel = results
+    assert err["cur"] <= 1e-8
+    assert rel["cur"] <= 6e-8
+
+
+def test_order_three_products_matter(results):
+    err, _ = results
+    assert err["six"] > 1.5 * err["cur"]
+
+
+def test_table_bound_grids_cost_little(results):
+    err, rel = results
+    assert err["bound"] <= max(5.0 * err["cur"], 1e-10)
+    assert rel["bound"] <= 1.1 * rel["cur"]
