@@ -278,6 +278,8 @@ def main():
     ap.add_argument("--workload", default="si64")
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "bf16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="also time the adjoint (dL/dv, dL/dR) on the same plan")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
@@ -451,6 +453,23 @@ def main():
                 "max_abs_dH_vs_fp64_gpu": float((h - h64).abs().max().item()),
                 "density_rel_l2_vs_fp64_gpu": float(((n - n64).norm() / n64.norm()).item())}
 
+    # the adjoint of L = sum_k g_k h_k (dL/dv, dL/dR) on the same plan; it
+    # runs the FP64 path whatever the context's precision
+    adj = None
+    if args.adjoint_steps > 0:
+        g = torch.from_numpy(W.rng_for(3, W.PURPOSE_G).standard_normal(nnz)).to(dev)
+        dv = torch.empty(n_pts, dtype=torch.float64, device=dev)
+        dR = torch.empty((n_at, 3), dtype=torch.float64, device=dev)
+
+        def adj_step():
+            ctx.adjoint(g, v, dv, dR, ws=ws)
+
+        adj_step()
+        ctx.sync()
+        ta = timed(args.adjoint_steps, adj_step)
+        adj = {"ms_per_step": statistics.mean(ta), "value": n_pts / (statistics.mean(ta) * 1e-3),
+               "unit": UNIT, "path": "fp64", "steps": args.adjoint_steps}
+
     # many-instance: the FP64 path called molecule by molecule (one context
     # and plan per molecule, one shared workspace), on the same inputs
     fp64_loop = None
@@ -555,6 +574,7 @@ def main():
                        "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
                "gpu_launches": launches * args.steps if launches is not None else None,
                "fp64_path": fp64,
+               "adjoint": adj,
                "fp64_per_molecule_loop": fp64_loop,
                "errors_vs_oracle": errors,
                "clocks": clk.summary(),
