@@ -39,6 +39,8 @@ class FGIError(RuntimeError):
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libfgi.so and declare every entry point's argument and result types.
+    ImportError when the library is not built: there is no fallback."""
     if not os.path.exists(path):
         raise ImportError("libfgi.so is not built (run __graft_entry__.build()); "
                           "there is no fallback path")
@@ -81,6 +83,7 @@ _lib = None
 
 
 def lib() -> C.CDLL:
+    """The process-wide handle of libfgi.so (loaded on first use)."""
     global _lib
     if _lib is None:
         _lib = load_library()
@@ -129,6 +132,7 @@ class Context:
         self._ws = None
 
     def close(self):
+        """Free the context and its device storage (fgi_destroy); idempotent."""
         if self._h:
             self._lib.fgi_destroy(self._h)
             self._h = C.c_void_p()
@@ -145,6 +149,8 @@ class Context:
 
     # ---- inputs
     def add_radial(self, l: int, h: float, coef) -> int:
+        """Add a radial function u(r) as a uniform cubic spline: coef [n_knots-1][4]
+        on the knots r_k = k h (u = c0 + t (c1 + t (c2 + t c3))).  Returns its id."""
         coef = _np(coef, np.float64)
         out = C.c_int()
         self._check(self._lib.fgi_add_radial(self._h, int(l), float(h), coef.shape[0] + 1, _ptr(coef),
@@ -152,12 +158,16 @@ class Context:
         return out.value
 
     def add_species(self, Z: float, radial_ids) -> int:
+        """Add a species: nuclear charge Z and its shells (radial ids, 2l+1
+        functions each, m = -l..l).  Returns its id."""
         ids = _np(radial_ids, np.int32)
         out = C.c_int()
         self._check(self._lib.fgi_add_species(self._h, float(Z), len(ids), _ptr(ids), C.byref(out)))
         return out.value
 
     def set_systems(self, atom_off, species, xyz):
+        """Independent systems: atom_off [n_sys+1] splits species [n_atoms] and
+        xyz [n_atoms][3] (Bohr).  Invalidates the plan."""
         atom_off = _np(atom_off, np.int64)
         species = _np(species, np.int32)
         xyz = _np(xyz, np.float64)
@@ -166,6 +176,9 @@ class Context:
         self._n_sys = len(atom_off) - 1
 
     def set_grid(self, xyz, w, batch_off, batch_sys):
+        """Grid points xyz [n_pts][3] and weights w, grouped in batches of
+        consecutive points (batch_off [n_batch+1], at most 1024 points each),
+        batch_sys [n_batch] the system of each batch.  Invalidates the plan."""
         xyz = _np(xyz, np.float64)
         w = _np(w, np.float64)
         batch_off = _np(batch_off, np.int64)
@@ -175,11 +188,15 @@ class Context:
         self._n_batch = len(batch_off) - 1
 
     def plan(self, precision="fp64", tune_path=None):
+        """Build the plan (active functions, pattern, tile lists, device copies)
+        for precision 'fp64', 'split_bf16' or 'bf16'; tune_path: optional
+        settings file (see tune.py)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._check(self._lib.fgi_plan(self._h, p, tune_path.encode() if tune_path else None))
         self._ws = None
 
     def set_precision(self, precision):
+        """Switch the precision of later compute calls without re-planning."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._check(self._lib.fgi_set_precision(self._h, p))
 
@@ -195,11 +212,14 @@ class Context:
 
     # ---- queries
     def sizes(self):
+        """(n_fn, nnz, n_pts, n_atoms) over all systems."""
         v = [C.c_int64() for _ in range(4)]
         self._check(self._lib.fgi_get_sizes(self._h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)       # n_fn, nnz, n_pts, n_atoms
 
     def system(self, s: int):
+        """(fn0, n_fn, val0, nnz) of system s: its first function and count, and
+        its first stored value and count in the H / D arrays."""
         v = [C.c_int64() for _ in range(4)]
         self._check(self._lib.fgi_get_system(self._h, s, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)       # fn0, n_fn, val0, nnz
@@ -230,6 +250,8 @@ class Context:
         return out
 
     def pattern(self, s: int = 0):
+        """CSR pattern of system s's stored upper triangle: (rowptr [n_fn+1]
+        relative to val0, col [nnz] function index within the system)."""
         nnz = C.c_int64()
         rp = C.c_void_p()
         col = C.c_void_p()
@@ -241,11 +263,13 @@ class Context:
         return rowptr, cols
 
     def workspace_size(self) -> int:
+        """Bytes of device scratch the compute calls need (every precision)."""
         b = C.c_size_t()
         self._check(self._lib.fgi_workspace_size(self._h, C.byref(b)))
         return b.value
 
     def workspace(self):
+        """A cached uint8 device buffer of at least workspace_size() bytes."""
         need = self.workspace_size()
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda:%d" % self.device)
@@ -253,6 +277,10 @@ class Context:
 
     # ---- compute
     def integrate_h(self, v, h=None, accumulate=False, ws=None, stream=None):
+        """H values on the pattern: h (+)= sum_p w_p v_p phi_i phi_j for every
+        stored (i, j).  v: CUDA float64 [n_pts]; h: CUDA float64 [nnz]
+        (allocated when None); returns h.  Enqueued on `stream`; sync()
+        reports device-side errors."""
         n_fn, nnz, n_pts, _ = self.sizes()
         v = _dev_f64(v, n_pts, "v")
         if h is None:
@@ -264,6 +292,9 @@ class Context:
         return h
 
     def density(self, d, n=None, traces=None, ws=None, stream=None, with_traces=True):
+        """n_p = sum_ij phi_i(r_p) D_ij phi_j(r_p) from the stored values d of the
+        symmetric D (CUDA float64 [nnz]); returns (n [n_pts], traces [n_sys] =
+        sum_p w_p n_p per system, or None without traces)."""
         n_fn, nnz, n_pts, _ = self.sizes()
         d = _dev_f64(d, nnz, "d")
         if n is None:
@@ -278,6 +309,9 @@ class Context:
         return n, traces
 
     def adjoint(self, g, v, dv=None, dR=None, ws=None, stream=None):
+        """Gradients of L = sum_k g_k h_k(v, R) (g: CUDA float64 [nnz], the
+        gradient with respect to the stored H values): returns dv [n_pts] and
+        dR [n_atoms][3], grid and weights held fixed.  FP64 path."""
         n_fn, nnz, n_pts, n_at = self.sizes()
         g = _dev_f64(g, nnz, "g")
         v = _dev_f64(v, n_pts, "v")
@@ -291,6 +325,8 @@ class Context:
         return dv, dR
 
     def trace(self, a, b, out=None, stream=None):
+        """tr(A B) per system, in FP64, from the stored upper-triangle values of
+        two symmetric matrices on the pattern (e.g. tr(DS), tr(DH))."""
         _, nnz, _, _ = self.sizes()
         _dev_f64(a, nnz, "a")
         _dev_f64(b, nnz, "b")
@@ -300,6 +336,8 @@ class Context:
         return out
 
     def sync(self, stream=None):
+        """Wait for the stream and raise FGIError for a device-side error
+        (FGI_ERR_TIMEOUT, FGI_ERR_NONFINITE) recorded since the last sync."""
         self._check(self._lib.fgi_sync(self._h, _stream(stream)))
 
     def selftest_wait_timeout(self, stream=None):
@@ -308,9 +346,13 @@ class Context:
         self._check(self._lib.fgi_selftest_wait_timeout(self._h, _stream(stream)))
 
     def profile(self, enable: bool = True):
+        """Start (clearing the record) or stop timing every kernel launch with
+        CUDA events; not inside stream capture."""
         self._check(self._lib.fgi_profile(self._h, int(bool(enable))))
 
     def profile_read(self, kind):
+        """Launches, milliseconds, algorithmic flops and bytes recorded for a kernel
+        class: 'basis', 'h', 'density', 'adjoint' or 'other'."""
         k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
         n = C.c_int64()
         ms, fl, by = C.c_double(), C.c_double(), C.c_double()
@@ -335,16 +377,19 @@ class HIntegrate(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, context: Context, v, R):
+        """h = H(v, R) on the context's plan (R: the planned atom positions)."""
         fctx.context = context
         fctx.save_for_backward(v)
         return context.integrate_h(v.detach().contiguous())
 
     @staticmethod
     def backward(fctx, g):
+        """(None, dL/dv, dL/dR) from the adjoint kernels."""
         (v,) = fctx.saved_tensors
         dv, dR = fctx.context.adjoint(g.contiguous(), v.detach().contiguous())
         return None, dv, dR
 
 
 def integrate(context: Context, v, R):
+    """Differentiable h = H(v, R) (see HIntegrate)."""
     return HIntegrate.apply(context, v, R)
