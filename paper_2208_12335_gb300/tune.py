@@ -25,6 +25,8 @@ DEFAULT_CANDIDATES = [
     {"density_sb_points": 0},
     {"h_sb_points": 0},
     {"h_sb_points": 256, "h_sb_growth": 1.25},
+    {"h_sb_points": 700, "h_sb_growth": 1.25},
+    {"h_sb_points": 1024, "h_sb_growth": 1.25},
     {"density_sb_points": 512, "density_sb_growth": 1.35},
     {"density_sb_points": 768, "density_sb_growth": 1.35},
     {"density_sb_points": 1024, "density_sb_growth": 1.2},
