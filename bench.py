@@ -215,6 +215,18 @@ def oracle_sample(prob, D, n_batches, seed=7, keep=False):
     return out + ((sub, act, Hs, Ds, ns) if keep else ())
 
 
+def oracle_single_core(prob, D, n_batches=2, seed=3):
+    """The oracle on one thread over a small seeded sample: points/s."""
+    import oracle as O
+    n = O.num_threads()
+    O.set_num_threads(1)
+    try:
+        p, dt, _, _ = oracle_sample(prob, D, n_batches, seed=seed)
+    finally:
+        O.set_num_threads(n)
+    return p / dt
+
+
 def compare_on_sample(sample, precision, device, dev, torch, Context):
     """The library on the oracle's sample (the same sub-grid, planned on its
     own): max |dH| over the stored entries of system 0 and the density's
@@ -259,12 +271,14 @@ def run_reference(args, rank):
         pts_tot += p
         t_tot += dt
     value = pts_tot / t_tot
+    single = oracle_single_core(prob, D)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": desc, "n_pts": prob.n_pts},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                            "sample": "%d seeded batches of %d per step (H + density)" % (nb, prob.n_batch)},
+                            "sample": "%d seeded batches of %d per step (H + density)" % (nb, prob.n_batch),
+                            "single_core_value": single, "single_core_sample": "2 seeded batches, 1 thread"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -552,7 +566,9 @@ def main():
             res = oracle_sample(prob, D, args.ref_batches, keep=True)
             p, dt, thr, nbs = res[:4]
             cpu = {"value": p / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
-                   "sample": "%d seeded batches (%d points) of %d, H + density" % (nbs, p, prob.n_batch)}
+                   "sample": "%d seeded batches (%d points) of %d, H + density" % (nbs, p, prob.n_batch),
+                   "single_core_value": oracle_single_core(prob, D),
+                   "single_core_sample": "2 seeded batches, 1 thread"}
             if not args.no_check:
                 errors = compare_on_sample(res[4:], args.precision, local, dev, torch, Context)
         launches = int(sum(prof[k]["launches"] for k in prof) / args.steps) if prof else None

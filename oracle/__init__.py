@@ -66,12 +66,18 @@ def _load():
             lib.orc_adjoint.argtypes = [P, I64, P, P, P, C.c_int, P, P, P, P]
             lib.orc_adjoint.restype = C.c_int
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_set_num_threads.argtypes = [C.c_int]
             _lib = lib
     return _lib
 
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops (timing baselines only)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def _p(a):
