@@ -120,3 +120,42 @@ def test_table_bound_grids_cost_little(results):
     err, rel = results
     assert err["bound"] <= max(5.0 * err["cur"], 1e-10)
     assert rel["bound"] <= 1.1 * rel["cur"]
+
+
+def test_deeper_h_contractions_cost_little():
+    """Consecutive batches merged into H super-batches of up to 1024 points
+    (the deepest contraction the kernels take): the model's H error stays
+    within a small factor of the unmerged one on 16 consecutive batches of
+    the 1000-atom cluster."""
+    full = W.chno_cluster(atoms_with_grid=[0, 1])
+    prob = full.subgrid(np.arange(100, 116))
+    B = O.system_basis(prob)
+    act_all = O.active_functions(B, prob.pts)
+    pos = -np.ones(B.n_fn, np.int64)
+    pos[act_all] = np.arange(len(act_all))
+    sizes = np.diff(prob.batch_off)
+    err = {}
+    for pmax in (0, 1024):
+        groups, cur, cp = [], [], 0
+        for b in range(prob.n_batch):
+            if cur and (pmax == 0 or cp + sizes[b] > pmax):
+                groups.append(cur)
+                cur, cp = [], 0
+            cur.append(b)
+            cp += sizes[b]
+        groups.append(cur)
+        n = len(act_all)
+        Hx, Hm = np.zeros((n, n)), np.zeros((n, n))
+        for g in groups:
+            s0, s1 = prob.batch_off[g[0]], prob.batch_off[g[-1] + 1]
+            p = prob.pts[s0:s1]
+            wv = prob.w[s0:s1] * prob.v[s0:s1]
+            act = O.active_functions(B, p)
+            psi = O.phi(B, p, sub=act) * np.sqrt(np.abs(wv))[:, None]
+            unit = M.grid_units(np.abs(psi).max(axis=0), np.abs(psi).sum(axis=0), (len(p) + 63) // 64 * 64)
+            ix = np.ix_(pos[act], pos[act])
+            Hx[ix] -= psi.T @ psi
+            Hm[ix] -= M.h_block(psi, unit)
+        err[pmax] = np.abs(Hm - Hx).max()
+    assert err[1024] <= 3.0 * err[0] + 1e-10, err
+    assert err[1024] <= 1e-8
