@@ -8,8 +8,8 @@
 // terms x = x0 + x1 + x2: x0 a fixed-point digit on a power-of-two grid per
 // row (H) or per point (density), chosen so that every partial sum of
 // x0*y0 products is exact in FP32, and x1, x2 the BF16 split of the
-// remainder.  H accumulates the 8 products of combined order <= 3 except
-// x2*y2, the density the 6 of order <= 2; x0*y0 has its own FP32
+// remainder.  H and the density accumulate the 8 products of combined
+// order <= 3 except x2*y2; x0*y0 has its own FP32
 // accumulator in tensor memory, the others a second one.  Cross-batch sums:
 // H in 2^-40 fixed point (int64 atomics, deterministic), the density in
 // FP64.  n_split = 1 keeps x0*y0 only (plain BF16).
@@ -451,15 +451,18 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
         ipow[2] = df_mul(ipow[1], ipow[0]);
         ipow[3] = df_mul(ipow[2], ipow[0]);
         int f = 0;
-        // knot interval and offset, shared by consecutive shells on the same knot grid
-        float grid_hi = -1.f, grid_lo = 0.f, t = 0.f;
+        // knot interval and offset, shared by consecutive shells on the same
+        // knot grid; t = d/h - k kept as the unevaluated pair t + tl (the
+        // subtraction of the integer part is exact)
+        float grid_hi = -1.f, grid_lo = 0.f, t = 0.f, tl = 0.f;
         int grid_nk = -1, kk = 0;
         const float4 *sc = nullptr;            // species on one grid: this point's interval row
         if (S.shared_grid && !origin) {
             const df sd = df_mul(d, df{S.inv_h_hi, S.inv_h_lo});
             kk = (int)floorf(sd.hi);
             kk = max(0, min(kk, S.nk - 2));
-            t = (sd.hi - (float)kk) + sd.lo;
+            t = sd.hi - (float)kk;
+            tl = sd.lo;
             sc = P.scoef + S.scoef_off + 2 * ((long long)kk * S.n_shell);
         }
         for (int sh = 0; sh < S.n_shell; sh++) {
@@ -477,8 +480,10 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                         rad = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});
                     }
                 } else {
-                    // t = frac(d/h) from the double-float d; u = c0 + t (c1 + t (c2 + t c3))
-                    // with c0 in double-float and the (smaller) polynomial tail in FP32
+                    // t = frac(d/h) from the double-float d; u = c0 + t c1 + t^2 (c2 + t c3)
+                    // with c0 + t c1 in double-float and only the t^2 part in FP32: near
+                    // a nucleus u is mostly t c1 (u(0) = 0 for s shells), and an FP32
+                    // t c1 would carry its 2^-24 rounding into the largest densities
                     const float4 *ce;
                     if (sc) {
                         ce = sc + 2 * sh;
@@ -490,15 +495,21 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
                             const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
                             kk = (int)floorf(s.hi);
                             kk = max(0, min(kk, R.nk - 2));
-                            t = (s.hi - (float)kk) + s.lo;
+                            t = s.hi - (float)kk;
+                            tl = s.lo;
                         }
                         ce = P.coef_dd + 2 * (R.coef_off + kk);
                     }
                     const float4 ch = __ldg(ce);
-                    const float c0lo = __ldg(reinterpret_cast<const float *>(ce + 1));
-                    const float tail = t * (ch.y + t * (ch.z + t * ch.w));
-                    df uu = df_two_sum(ch.x, tail);
-                    uu = df_fast_two_sum(uu.hi, uu.lo + c0lo);
+                    const float4 cl = __ldg(ce + 1);
+                    // t c1 with t = t + tl, c1 = ch.y + cl.y: exact product of the high
+                    // parts plus the two cross terms
+                    const df lin = df_two_prod(t, ch.y);
+                    const float lin_lo = fmaf(t, cl.y, fmaf(tl, ch.y, lin.lo));
+                    const float quad = (t * t) * fmaf(t, ch.w, ch.z);
+                    df uu = df_two_sum(ch.x, lin.hi);
+                    // the t^2 part may exceed c0 + t c1 (p and d shells near a nucleus)
+                    uu = df_two_sum(uu.hi, uu.lo + ((cl.x + lin_lo) + quad));
                     const df ip = R.l == 0 ? ipow[0] : (R.l == 1 ? ipow[1] : (R.l == 2 ? ipow[2] : ipow[3]));
                     rad = df_mul(uu, ip);
                 }
@@ -846,9 +857,11 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
                     const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
                     if (d >= R.rcut_f * 1.00001f) continue;
                     const int ki = min(max((int)(dl * R.inv_h_hi), 0), R.nk - 2);
-                    const float b = fminf(__ldg(P.rbound + R.bound_off + ki) * ymax[R.l], 1.0e30f);
-                    mx = fmaxf(mx, b);
-                    sm += (float)(2 * R.l + 1) * b;
+                    const float tb = __ldg(P.rbound + R.bound_off + ki);
+                    mx = fmaxf(mx, fminf(tb * ymax[R.l], 1.0e30f));
+                    // sum over m of |Y_lm| <= (2l+1)/sqrt(4 pi): Cauchy-Schwarz with
+                    // sum_m Y_lm^2 = (2l+1)/(4 pi) (Unsold's theorem)
+                    sm += fminf(tb * (float)(2 * R.l + 1) * (0.28209479f * 1.000001f), 1.0e30f);
                 }
                 if (!(sm < 1.0e30f)) sm = 1.0e30f;
                 atomicMax(&colmax[k], __float_as_uint(mx));
@@ -956,10 +969,11 @@ constexpr int kWarpProducer = 8, kWarpMma = 9;
 constexpr int kEpiThreads = 256;
 constexpr int kStages = 2;
 constexpr int kStageBytes = 6 * kChunkBytes;     // A and B operands, 3 planes each
-#ifndef FGI_DENSITY_ORDER
-#define FGI_DENSITY_ORDER 2
-#endif
-constexpr int kDensityOrder = FGI_DENSITY_ORDER;  // split products kept in the density (6 of 9)
+// split products kept in the density: combined order <= 3 except x2*y2 (8 of
+// 9), as in H; the order-3 pair x1*y2, x2*y1 is about 2^-27 of the leading
+// product, which over ~10^3 functions is no longer far below the 1e-7
+// relative bound on n
+constexpr int kDensityOrder = 3;
 
 struct ColRef {                                  // column i of an H tile (a row of the stored triangle)
     long long rpl;                               // first stored value of row i minus i's index in its atom

@@ -174,6 +174,12 @@ class Context:
         self._check(self._lib.fgi_set_systems(self._h, len(atom_off) - 1, _ptr(atom_off), _ptr(species),
                                               _ptr(xyz)))
         self._n_sys = len(atom_off) - 1
+        self._xyz = xyz.reshape(-1, 3).copy()
+
+    def positions(self):
+        """The atom positions [n_atoms][3] (Bohr) given to set_systems: the
+        geometry the plan and every H integration are for."""
+        return self._xyz.copy()
 
     def set_grid(self, xyz, w, batch_off, batch_sys):
         """Grid points xyz [n_pts][3] and weights w, grouped in batches of
@@ -377,7 +383,15 @@ class HIntegrate(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, context: Context, v, R):
-        """h = H(v, R) on the context's plan (R: the planned atom positions)."""
+        """h = H(v, R) on the context's plan.  R must equal the planned atom
+        positions: the plan (active functions, pattern) belongs to one
+        geometry, so a moved R raises ValueError instead of returning H at
+        the old positions; plan a new context for a new geometry."""
+        planned = torch.as_tensor(context.positions(), dtype=torch.float64)
+        Rc = R.detach().to("cpu", torch.float64).reshape(planned.shape)
+        if not torch.equal(Rc, planned):
+            raise ValueError("HIntegrate: R differs from the planned atom positions by up to %.3e Bohr; "
+                             "plan a context for the new geometry" % float((Rc - planned).abs().max()))
         fctx.context = context
         fctx.save_for_backward(v)
         return context.integrate_h(v.detach().contiguous())

@@ -12,5 +12,8 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # long-running tests last, so that a quick failure elsewhere shows first
-    items.sort(key=lambda it: it.get_closest_marker("slow") is not None)
+    # long-running tests after the others, so that a quick failure elsewhere
+    # shows first; the test_zz_* files (single-purpose entry points) at the
+    # very end, after the slow tests too
+    items.sort(key=lambda it: (os.path.basename(str(it.fspath)).startswith("test_zz"),
+                               it.get_closest_marker("slow") is not None))

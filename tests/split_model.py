@@ -75,12 +75,15 @@ def h_block(psi, unit, n_products=8):
     return x0.T @ x0 + _fp32_steps(pairs, psi.shape[0])
 
 
-def density_e(D, dunit, Phi, punit):
+def density_e(D, dunit, Phi, punit, n_products=8):
     """E = D Phi (functions x points): D rows on `dunit`, Phi columns (points)
-    on `punit`, the 6 products of order <= 2."""
+    on `punit`; the 8 products of combined order <= 3 except d2 p2 (as the
+    kernels), or the 6 of order <= 2."""
     d0, d1, d2 = split3(D, dunit[:, None])
     p0, p1, p2 = split3(Phi, punit[None, :])
     pairs = [(d0, p1), (d1, p0), (d0, p2), (d1, p1), (d2, p0)]
+    if n_products == 8:
+        pairs += [(d1, p2), (d2, p1)]
     return d0 @ p0 + _fp32_steps(pairs, D.shape[1])
 
 

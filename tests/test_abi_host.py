@@ -291,3 +291,21 @@ def test_every_autotuner_candidate_plans(fgi, water, tmp_path):
         ctx = host_ctx(fgi, water)
         ctx.plan("split_bf16", str(path))
         assert ctx.workspace_size() > 0
+
+
+def test_autograd_forward_refuses_a_moved_geometry(fgi, water):
+    """The plan belongs to the positions given to set_systems: the
+    differentiable H call refuses an R that differs from them (before any
+    device work), rather than returning H at the planned positions."""
+    import torch
+    ctx = fgi.Context(-1).load(water, "fp64")
+    assert np.array_equal(ctx.positions(), water.atom_xyz)
+    v = torch.from_numpy(water.v)
+    R = torch.from_numpy(water.atom_xyz.copy())
+    R[1, 2] += 1e-6
+    with pytest.raises(ValueError, match="planned atom positions"):
+        fgi.integrate(ctx, v, R)
+    # at the planned positions the call goes on to the H integration, whose
+    # argument check wants a device tensor
+    with pytest.raises(TypeError, match="CUDA"):
+        fgi.integrate(ctx, v, torch.from_numpy(water.atom_xyz.copy()))

@@ -728,20 +728,27 @@ def merge_problems(name, parts, workload_index):
 # matrices that enter the method as inputs
 # --------------------------------------------------------------------------
 
+def occupied_orbitals(n_fn: int, n_occ: int, rng: np.random.Generator):
+    """C: the first n_occ columns of a seeded orthonormal matrix (QR of a
+    Gaussian matrix, signs fixed by R's diagonal)."""
+    q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
 def density_matrix_occ(n_fn: int, n_occ: int, rng: np.random.Generator, occ: float = 2.0):
     """D = occ * C C^T, C = first n_occ columns of a seeded orthonormal matrix."""
-    q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
-    q = q * np.sign(np.diag(r))[None, :]
+    q = occupied_orbitals(n_fn, n_occ, rng)
     return occ * (q @ q.T), q
 
 
 def density_values_occ(n_fn: int, n_occ: int, rows, cols, rng: np.random.Generator, occ: float = 2.0,
-                       accel=None, chunk_bytes: int = 1 << 30):
+                       accel=None, chunk_bytes: int = 1 << 30, q=None):
     """The stored values D[rows, cols] of D = occ C C^T (C as in
     density_matrix_occ) without forming the dense n x n matrix; the row
-    dot products run with torch on `accel` when given."""
-    q, r = np.linalg.qr(rng.standard_normal((n_fn, n_occ)))
-    q = q * np.sign(np.diag(r))[None, :]
+    dot products run with torch on `accel` when given.  q: C itself, when
+    the caller already drew it (rng is then unused)."""
+    if q is None:
+        q = occupied_orbitals(n_fn, n_occ, rng)
     chunk = max(1, chunk_bytes // (8 * max(1, n_occ)))
     out = np.empty(len(rows))
     if accel is not None:
