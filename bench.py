@@ -56,6 +56,15 @@ def make_workload(name, accel=None):
     raise SystemExit("unknown workload " + name)
 
 
+def gen_backend():
+    """'cuda' when a CUDA device is present (input generation only), else None."""
+    try:
+        import torch
+        return "cuda" if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
 def density_matrix(prob, rng):
     n = prob.n_fn_sys(0)
     if n <= 4000:
@@ -255,11 +264,37 @@ def compare_on_sample(sample, precision, device, dev, torch, Context):
     return res
 
 
+def executed_tensor_flops(ctx, products):
+    """BF16 tensor-core FLOPs one step (H + density) executes, from the
+    plan's schedules: 128 x 128 output tiles, contraction depth in chunks
+    of 64, padding included; H over the upper tile triangle, the density
+    over the upper block triangle of D."""
+    tot = 0.0
+    sh = ctx.schedule("h")
+    for P_, n_, rank in zip(sh["sb_points"], sh["sb_fns"], sh["sb_rank"]):
+        if rank < 0:
+            continue
+        nrb, nc = -(-int(n_) // 128), -(-int(P_) // 64)
+        tot += nrb * (nrb + 1) / 2 * 2.0 * 128 * 128 * nc * 64
+    sd = ctx.schedule("density")
+    for P_, n_, rank in zip(sd["sb_points"], sd["sb_fns"], sd["sb_rank"]):
+        if rank < 0:
+            continue
+        nrb, nkc, nc = -(-int(n_) // 128), -(-int(n_) // 64), -(-int(P_) // 64)
+        tiles = (nc + 1) // 2
+        for J in range(nrb):
+            tot += tiles * 2.0 * 128 * 128 * (nkc - 2 * J) * 64
+    return tot * products
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
     if rank != 0:
         return
-    prob, desc = make_workload(args.workload)
+    # the same generator backend as the library's arm (partition weights and
+    # potential with torch on the device when one is present), so that both
+    # arms integrate bit-identical inputs
+    prob, desc = make_workload(args.workload, accel=gen_backend())
     D = density_matrix(prob, W.rng_for(1, W.PURPOSE_D))
     nb = args.ref_batches
     for _ in range(args.warmup):
@@ -286,18 +321,24 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="si64")
+    ap.add_argument("--workload", default="chno1000")
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "bf16", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--bf16-steps", type=int, default=2,
+                    help="also time the plain BF16 variant and state its error (0: skip)")
+    ap.add_argument("--many", type=int, default=512,
+                    help="also run the many-instance workload of this many molecules (split BF16 in one "
+                         "captured graph against a per-molecule FP64 loop); 0: skip")
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="also time the adjoint (dL/dv, dL/dR) on the same plan")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
-    ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
+    ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
+                    help="replay the step as a captured CUDA graph (default)")
     ap.add_argument("--fp64-per-system", action="store_true",
                     help="many-instance workloads: also time the FP64 path called molecule by molecule")
     ap.add_argument("--batches", type=int, default=0,
@@ -322,7 +363,9 @@ def main():
     dev = torch.device("cuda:%d" % local)
     from paper_2208_12335_gb300 import Context
 
+    t0 = time.perf_counter()
     prob, desc = make_workload(args.workload, accel="cuda")
+    gen_s = time.perf_counter() - t0
     if args.batches:
         ids = np.sort(np.random.default_rng(99).choice(prob.n_batch, size=min(args.batches, prob.n_batch),
                                                         replace=False))
@@ -450,13 +493,15 @@ def main():
     e2e_times = timed(max(3, args.steps // 2), e2e_step)
     e2e_ms = statistics.mean(e2e_times)
 
-    # FP64 GPU path on the same inputs (the comparator)
+    # FP64 GPU path on the same inputs (the comparator); its first step is
+    # timed too (at tens of seconds per step, a warm-up step would double
+    # the bench's run time for nothing: nothing is compiled at run time)
     fp64 = None
+    h64 = n64 = None
     if args.precision != "fp64" and args.fp64_steps > 0:
         ctx.set_precision("fp64")
-        step()
-        ctx.sync()
         t64 = timed(args.fp64_steps, step)
+        ctx.sync()
         h64 = h.clone()
         n64 = n.clone()
         ctx.set_precision(args.precision)
@@ -466,6 +511,23 @@ def main():
                 "value": n_pts / (statistics.mean(t64) * 1e-3),
                 "max_abs_dH_vs_fp64_gpu": float((h - h64).abs().max().item()),
                 "density_rel_l2_vs_fp64_gpu": float(((n - n64).norm() / n64.norm()).item())}
+
+    # the plain BF16 variant on the same inputs: its time and its error
+    # against the FP64 GPU path (every entry) and, below, the oracle sample
+    bf16 = None
+    if args.precision == "split_bf16" and args.bf16_steps > 0:
+        ctx.set_precision("bf16")
+        step()
+        ctx.sync()
+        tb = timed(args.bf16_steps, step)
+        ctx.sync()
+        bf16 = {"ms_per_step": statistics.mean(tb), "value": n_pts / (statistics.mean(tb) * 1e-3)}
+        if h64 is not None:
+            bf16["max_abs_dH_vs_fp64_gpu"] = float((h - h64).abs().max().item())
+            bf16["density_rel_l2_vs_fp64_gpu"] = float(((n - n64).norm() / n64.norm()).item())
+        ctx.set_precision(args.precision)
+        step()
+        ctx.sync()
 
     # the adjoint of L = sum_k g_k h_k (dL/dv, dL/dR) on the same plan; it
     # runs the FP64 path whatever the context's precision
@@ -483,6 +545,100 @@ def main():
         ta = timed(args.adjoint_steps, adj_step)
         adj = {"ms_per_step": statistics.mean(ta), "value": n_pts / (statistics.mean(ta) * 1e-3),
                "unit": UNIT, "path": "fp64", "steps": args.adjoint_steps}
+
+    def many_leg(n_mol):
+        """The many-instance workload: n_mol independent molecules in one plan,
+        the split-BF16 step (H + density of every molecule) replayed as one
+        captured CUDA graph, against the FP64 path called molecule by
+        molecule on the same GPU (one context per molecule, one shared
+        workspace); errors per molecule against that loop, and of molecule
+        0 against the oracle on a sample of its batches."""
+        t0 = time.perf_counter()
+        mp, mdesc = make_workload("many%d" % n_mol, accel="cuda")
+        mgen = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mc = Context(local).load(mp, "split_bf16")
+        mplan = time.perf_counter() - t0
+        _, m_nnz, m_pts, _ = mc.sizes()
+        rng = W.rng_for(4, W.PURPOSE_D)
+        mdv = np.zeros(m_nnz)
+        D0 = None
+        for s_ in range(mp.n_sys):
+            _, nf, val0, nn = mc.system(s_)
+            Ds, _ = W.density_matrix_occ(nf, max(1, int(round(0.28 * nf))), rng)
+            mdv[val0:val0 + nn] = stored_values(mc, Ds, s_)[0]
+            if s_ == 0:
+                D0 = Ds
+        mv = torch.from_numpy(mp.v).to(dev)
+        md = torch.from_numpy(mdv).to(dev)
+        mh = torch.empty(m_nnz, dtype=torch.float64, device=dev)
+        mn = torch.empty(m_pts, dtype=torch.float64, device=dev)
+        mtr = torch.empty(mp.n_sys, dtype=torch.float64, device=dev)
+        mws = mc.workspace()
+
+        def mstep():
+            mc.integrate_h(mv, mh, ws=mws)
+            mc.density(md, mn, mtr, ws=mws)
+
+        s2 = torch.cuda.Stream()
+        with torch.cuda.stream(s2):
+            mstep()
+        torch.cuda.synchronize()
+        mg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(mg):
+            mstep()
+        for _ in range(args.warmup):
+            mg.replay()
+        mc.sync()
+        tm = timed(max(3, args.steps // 2), mg.replay)
+        mc.sync()
+        ms_many = statistics.mean(tm)
+        # the per-molecule FP64 loop
+        subs = [mp.system_problem(s_) for s_ in range(mp.n_sys)]
+        ctxs = [Context(local).load(sp, "fp64") for sp in subs]
+        ws64 = torch.empty(max(256, max(cx.workspace_size() for cx in ctxs)), dtype=torch.uint8, device=dev)
+        ins = []
+        for s_, (sp, cx) in enumerate(zip(subs, ctxs)):
+            _, _, val0, nn = mc.system(s_)
+            ins.append((torch.from_numpy(sp.v).to(dev), md[val0:val0 + nn].contiguous(),
+                        torch.empty(nn, dtype=torch.float64, device=dev),
+                        torch.empty(sp.n_pts, dtype=torch.float64, device=dev)))
+
+        def loop_step():
+            for cx, (vs, ds, hs, ns) in zip(ctxs, ins):
+                cx.integrate_h(vs, hs, ws=ws64)
+                cx.density(ds, ns, ws=ws64, with_traces=False)
+
+        tl = timed(1, loop_step)
+        for cx in ctxs:
+            cx.sync()
+        dh_max, dn_max, dn_tot, n_tot = 0.0, 0.0, 0.0, 0.0
+        for s_, (_, _, hs, ns) in enumerate(ins):
+            _, _, val0, nn = mc.system(s_)
+            pts_s = torch.from_numpy(mp.system_points(s_)).to(dev)
+            dh_max = max(dh_max, float((mh[val0:val0 + nn] - hs).abs().max().item()))
+            dn = float((mn[pts_s] - ns).norm().item())
+            nr = float(ns.norm().item())
+            dn_max = max(dn_max, dn / nr)
+            dn_tot += dn * dn
+            n_tot += nr * nr
+        for cx in ctxs:
+            cx.close()
+        out = {"workload": mdesc, "n_systems": mp.n_sys, "n_pts": int(m_pts), "gen_s": round(mgen, 1),
+               "plan_s": round(mplan, 3), "graph": True,
+               "ms_per_step": ms_many, "value": m_pts / (ms_many * 1e-3), "unit": UNIT,
+               "fp64_per_molecule_loop": {"ms_per_step": statistics.mean(tl),
+                                          "value": m_pts / (statistics.mean(tl) * 1e-3),
+                                          "n_contexts": len(ctxs)},
+               "speedup_vs_fp64_per_molecule_loop": statistics.mean(tl) / ms_many,
+               "max_abs_dH_vs_fp64_loop": dh_max,
+               "density_rel_l2_vs_fp64_loop": (dn_tot / n_tot) ** 0.5,
+               "density_rel_l2_vs_fp64_loop_worst_molecule": dn_max}
+        mc.close()
+        return out, (mp, D0)
+
+    many, many_inputs = (many_leg(args.many) if args.many > 0 and args.workload != "many%d" % args.many
+                         else (None, None))
 
     # many-instance: the FP64 path called molecule by molecule (one context
     # and plan per molecule, one shared workspace), on the same inputs
@@ -540,8 +696,8 @@ def main():
                     r = {"kernel": kind, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                          "peak_note": "measured FP64 GEMM (cuBLAS) on this GPU"}
                 else:
-                    # BF16 products per algorithmic FLOP: split H 8, split density 6
-                    products = ({"h": 8, "density": 6}[kind] if args.precision == "split_bf16" else 1)
+                    # BF16 products per algorithmic FLOP: 8 for the split H and density
+                    products = 8 if args.precision == "split_bf16" else 1
                     r = {"kernel": kind, "bound": "tensor", "achieved": ach,
                          "peak": peaks["bf16_tflops_sustained"] / products, "unit": "TFLOP/s",
                          "peak_note": "%s sustained BF16 / %d BF16 products per algorithmic FLOP"
@@ -571,6 +727,17 @@ def main():
                    "single_core_sample": "2 seeded batches, 1 thread"}
             if not args.no_check:
                 errors = compare_on_sample(res[4:], args.precision, local, dev, torch, Context)
+                if bf16 is not None:
+                    # the plain BF16 variant on the same oracle sample
+                    eb = compare_on_sample(res[4:], "bf16", local, dev, torch, Context)
+                    bf16["max_abs_dH_vs_oracle_sample"] = eb["max_abs_dH_sample"]
+                    bf16["density_rel_l2_vs_oracle_sample"] = eb["density_rel_l2_sample"]
+                if many_inputs is not None:
+                    # molecule 0 of the many-instance workload against the oracle
+                    mp, D0 = many_inputs
+                    rm = oracle_sample(mp, D0, args.ref_batches, keep=True)
+                    many["molecule0_vs_oracle"] = compare_on_sample(rm[4:], "split_bf16", local, dev, torch,
+                                                                    Context)
         launches = int(sum(prof[k]["launches"] for k in prof) / args.steps) if prof else None
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -581,7 +748,7 @@ def main():
                "config": {"workload": desc, "n_pts": n_pts, "n_fn": n_fn, "nnz": nnz, "n_atoms": n_at,
                           "n_batches": prob.n_batch, "precision": args.precision,
                           "l2": "flushed between steps (256 MiB write)",
-                          "graph": bool(args.graph), "plan_s": round(plan_s, 3)},
+                          "graph": bool(args.graph), "plan_s": round(plan_s, 3), "gen_s": round(gen_s, 1)},
                "tflops": flops_step / (ms_max * 1e-3) / 1e12 if flops_step else None,
                "roofline": roof,
                "roofline_by_kernel": roof_all,
@@ -590,6 +757,8 @@ def main():
                        "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
                "gpu_launches": launches * args.steps if launches is not None else None,
                "fp64_path": fp64,
+               "bf16_path": bf16,
+               "many_instance": many,
                "adjoint": adj,
                "fp64_per_molecule_loop": fp64_loop,
                "errors_vs_oracle": errors,
@@ -597,6 +766,16 @@ def main():
                "profile_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof} if prof else None}
         if fp64:
             out["speedup_vs_fp64_gpu"] = fp64["ms_per_step"] / ms_max
+        if args.precision != "fp64":
+            # executed tensor-core work of the whole step against the measured
+            # sustained BF16 rate (padding of the 128 x 128 tiles included)
+            ex = executed_tensor_flops(ctx, 8 if args.precision == "split_bf16" else 1)
+            out["tensor_pipe"] = {"executed_bf16_tflop_per_step": ex / 1e12,
+                                  "achieved_tflops": ex / (ms_max * 1e-3) / 1e12,
+                                  "peak_tflops": peaks["bf16_tflops_sustained"],
+                                  "frac_of_sustained": ex / (ms_max * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
+                                  "note": "%s sustained BF16; whole step (basis, scatter and gathers included)"
+                                          % peak_src}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
