@@ -332,8 +332,8 @@ def main():
     ap.add_argument("--many", type=int, default=512,
                     help="also run the many-instance workload of this many molecules (split BF16 in one "
                          "captured graph against a per-molecule FP64 loop); 0: skip")
-    ap.add_argument("--adjoint-steps", type=int, default=0,
-                    help="also time the adjoint (dL/dv, dL/dR) on the same plan")
+    ap.add_argument("--adjoint-steps", type=int, default=2,
+                    help="also time the adjoint (dL/dv, dL/dR) on the same plan (0: skip)")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
@@ -512,25 +512,28 @@ def main():
                 "max_abs_dH_vs_fp64_gpu": float((h - h64).abs().max().item()),
                 "density_rel_l2_vs_fp64_gpu": float(((n - n64).norm() / n64.norm()).item())}
 
-    # the plain BF16 variant on the same inputs: its time and its error
-    # against the FP64 GPU path (every entry) and, below, the oracle sample
-    bf16 = None
+    # the cheaper plain BF16 variant (one product per algorithmic FLOP) on
+    # the same inputs: its time and its error against the FP64 GPU path
+    # (every entry) and, below, the oracle sample
+    variants = {}
     if args.precision == "split_bf16" and args.bf16_steps > 0:
-        ctx.set_precision("bf16")
-        step()
-        ctx.sync()
-        tb = timed(args.bf16_steps, step)
-        ctx.sync()
-        bf16 = {"ms_per_step": statistics.mean(tb), "value": n_pts / (statistics.mean(tb) * 1e-3)}
-        if h64 is not None:
-            bf16["max_abs_dH_vs_fp64_gpu"] = float((h - h64).abs().max().item())
-            bf16["density_rel_l2_vs_fp64_gpu"] = float(((n - n64).norm() / n64.norm()).item())
+        for prec in ("bf16",):
+            ctx.set_precision(prec)
+            step()
+            ctx.sync()
+            tb = timed(args.bf16_steps, step)
+            ctx.sync()
+            r = {"ms_per_step": statistics.mean(tb), "value": n_pts / (statistics.mean(tb) * 1e-3)}
+            if h64 is not None:
+                r["max_abs_dH_vs_fp64_gpu"] = float((h - h64).abs().max().item())
+                r["density_rel_l2_vs_fp64_gpu"] = float(((n - n64).norm() / n64.norm()).item())
+            variants[prec] = r
         ctx.set_precision(args.precision)
         step()
         ctx.sync()
 
-    # the adjoint of L = sum_k g_k h_k (dL/dv, dL/dR) on the same plan; it
-    # runs the FP64 path whatever the context's precision
+    # the adjoint of L = sum_k g_k h_k (dL/dv, dL/dR) on the same plan, in
+    # the context's precision (tensor cores for the split paths)
     adj = None
     if args.adjoint_steps > 0:
         g = torch.from_numpy(W.rng_for(3, W.PURPOSE_G).standard_normal(nnz)).to(dev)
@@ -544,7 +547,8 @@ def main():
         ctx.sync()
         ta = timed(args.adjoint_steps, adj_step)
         adj = {"ms_per_step": statistics.mean(ta), "value": n_pts / (statistics.mean(ta) * 1e-3),
-               "unit": UNIT, "path": "fp64", "steps": args.adjoint_steps}
+               "unit": UNIT, "path": args.precision, "steps": args.adjoint_steps,
+               "what": "dL/dv and dL/dR of L = sum_k g_k h_k, seeded random g on the H pattern"}
 
     def many_leg(n_mol):
         """The many-instance workload: n_mol independent molecules in one plan,
@@ -727,11 +731,11 @@ def main():
                    "single_core_sample": "2 seeded batches, 1 thread"}
             if not args.no_check:
                 errors = compare_on_sample(res[4:], args.precision, local, dev, torch, Context)
-                if bf16 is not None:
-                    # the plain BF16 variant on the same oracle sample
-                    eb = compare_on_sample(res[4:], "bf16", local, dev, torch, Context)
-                    bf16["max_abs_dH_vs_oracle_sample"] = eb["max_abs_dH_sample"]
-                    bf16["density_rel_l2_vs_oracle_sample"] = eb["density_rel_l2_sample"]
+                for prec, r in variants.items():
+                    # the cheaper variants on the same oracle sample
+                    eb = compare_on_sample(res[4:], prec, local, dev, torch, Context)
+                    r["max_abs_dH_vs_oracle_sample"] = eb["max_abs_dH_sample"]
+                    r["density_rel_l2_vs_oracle_sample"] = eb["density_rel_l2_sample"]
                 if many_inputs is not None:
                     # molecule 0 of the many-instance workload against the oracle
                     mp, D0 = many_inputs
@@ -742,7 +746,8 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": {"split_bf16": "split-bf16x3 (f32 acc, f64 cross-batch)", "bf16": "bf16 (f32 acc)",
+               "dtype": {"split_bf16": "split-bf16x3 (f32 acc, f64 cross-batch)",
+                         "bf16": "bf16 (f32 acc)",
                          "fp64": "f64"}[args.precision],
                "data": "synthetic",
                "config": {"workload": desc, "n_pts": n_pts, "n_fn": n_fn, "nnz": nnz, "n_atoms": n_at,
@@ -757,7 +762,7 @@ def main():
                        "h2d_bytes_per_step": 8 * (n_pts + nnz), "d2h_bytes_per_step": 8 * (nnz + n_pts)},
                "gpu_launches": launches * args.steps if launches is not None else None,
                "fp64_path": fp64,
-               "bf16_path": bf16,
+               "bf16_path": variants.get("bf16"),
                "many_instance": many,
                "adjoint": adj,
                "fp64_per_molecule_loop": fp64_loop,

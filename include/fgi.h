@@ -203,11 +203,16 @@ int fgi_integrate_h(fgi_ctx *ctx, const double *v_dev, double *h_dev, int accumu
    The paper has no counterpart: this is a packaging of fgi_integrate_h.
    Same arguments and results as fgi_integrate_h, but the scratch space is a
    static device array of FGI_STATIC_SCRATCH_BYTES inside the library, which
-   every GPU that loads the library keeps until the process exits; the call
-   itself allocates nothing (no cudaMalloc, cudaFree or library allocation).
+   every GPU holding the library's device code keeps until the process
+   exits; the call itself allocates nothing (no cudaMalloc, cudaFree or
+   library allocation).
    - The first call on a device looks up the array's device address (once,
      with that device current); make that first call before any stream
-     capture.
+     capture.  With CUDA's lazy module loading (the default in recent CUDA
+     releases) that first look-up may be what loads this part of the library
+     onto the device and reserves the array there: the first call can then
+     fail for lack of device memory (reported as FGI_ERR_CUDA), and only
+     devices on which the call has run hold the array.
    - A plan whose fgi_workspace_size() exceeds FGI_STATIC_SCRATCH_BYTES is
      rejected with FGI_ERR_WORKSPACE and a message giving both sizes.
    - All calls on a device share the one array, which keeps the last call's
@@ -232,10 +237,19 @@ int fgi_density(fgi_ctx *ctx, const double *d_dev, double *n_dev, double *traces
    G_ii = g_ii, G_ij = G_ji = g_ij/2, and the grid held fixed while atoms move,
      dv_dev[p]   = w_p sum_ij G_ij phi_i phi_j                      [n_pts]
      dR_dev[a,:] = -2 sum_p w_p v_p sum_{i on a} grad phi_i . (G phi)_i  [n_atoms][3]
-   v_dev is the potential of the forward call.  All device FP64.  The
-   adjoint is computed on the FP64 path whatever the context's precision;
-   the basis and its gradient are recomputed per batch (nothing is kept from
-   the forward call). */
+   v_dev is the potential of the forward call.  All device FP64.  The basis
+   and its gradient are recomputed per batch (nothing is kept from the
+   forward call).  FP64 contexts compute everything in FP64.  Split-BF16
+   (and plain BF16) contexts use the density's tensor-core tiles: G is
+   gathered per batch in full, E = G Phi is contracted on tcgen05 with the
+   context's split, dv_dev = w . sum_j phi_j E_j in double-float, and dR_dev
+   from E (kept in FP32) and FP32 basis gradients on CUDA cores; dR_dev is
+   summed with FP64 atomics (not bitwise reproducible).  Errors against the
+   FP64 oracle: max |d dv| / max |dv| <= 1e-7 and max |d dR| / max |dR| <= 1e-6
+   on the tested workloads (split).  The reading of the method behind the
+   adjoint (grid points, weights and v held fixed while atoms move, "a
+   Pulay-force-like term") is the one the forward integration fixes; the
+   paper prints no formula for it. */
 int fgi_adjoint(fgi_ctx *ctx, const double *g_dev, const double *v_dev, double *dv_dev,
                 double *dR_dev, void *ws, size_t ws_bytes, void *stream);
 

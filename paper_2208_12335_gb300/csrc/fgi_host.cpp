@@ -139,6 +139,7 @@ struct fgi_ctx {
     int *d_status = nullptr;
     TcPlan tc;                                // tensor-core plan of the H integration (the batches as given)
     TcPlan tcd;                               // tensor-core plan of the density (super-batches)
+    TcPlan tca;                               // the density's super-batches with room for E (the adjoint)
     // per-kernel CUDA-event profile
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -188,6 +189,7 @@ void free_device(fgi_ctx *c)
     c->arena_bytes = 0;
     tc_free(c->tc);
     tc_free(c->tcd);
+    tc_free(c->tca);
     c->planned = false;
 }
 
@@ -222,7 +224,7 @@ struct TuneSettings {
     long long wave_mb = 0;      // 0: the library default
     int h_sb_points = 400;      // merges small neighbouring batches; no deeper K than the largest batches
     double h_sb_growth = 1.25;
-    int bound_grids = 0;
+    int bound_grids = 2;        // table-bound digit grids for the H and density images
 };
 
 int read_tune_file(const char *path, TuneSettings &t, std::string *err)
@@ -313,7 +315,10 @@ int build_tc_plans(fgi_ctx *c, TcPlanInput tin, std::string *err)
     if (rc != FGI_OK) return rc;
     tin.sb_points = ts.sb_points;
     tin.sb_growth = ts.sb_growth;
-    return tc_build(c->tcd, tin, err);
+    rc = tc_build(c->tcd, tin, err);
+    if (rc != FGI_OK) return rc;
+    tin.with_e = true;                   // the adjoint: the density's tiles plus room for E = G Phi
+    return tc_build(c->tca, tin, err);
 }
 
 // ------------------------------------------------------------ plan building
@@ -607,7 +612,22 @@ int build_plan(fgi_ctx *c, const char *tune_path)
                 }
         }
         shell_rad.insert(shell_rad.end(), s.shells.begin(), s.shells.end());
+        d.lmax = 0;
+        for (int sh : s.shells) d.lmax = std::max(d.lmax, c->radials[sh].l);
         dsp.push_back(d);
+    }
+    std::vector<DevShell> dshell;
+    for (int r : shell_rad) {
+        const DevRadial &R = drad[r];
+        DevShell q{};
+        q.coef_off = (int)R.coef_off;
+        q.nk = R.nk;
+        q.l = R.l;
+        q.rcut_f = R.rcut_f;
+        q.inv_h_hi = R.inv_h_hi;
+        q.inv_h_lo = R.inv_h_lo;
+        q.bound_off = (int)R.bound_off;
+        dshell.push_back(q);
     }
     if (scoef.empty()) scoef.assign(8, 0.f);
     BigVec<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
@@ -657,6 +677,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_aloc = add(c->atom_loc.data(), c->atom_loc.size() * 4),
            i_sp = add(dsp.data(), dsp.size() * sizeof(DevSpecies)),
            i_shr = add(shell_rad.data(), shell_rad.size() * 4),
+           i_dsh = add(dshell.data(), dshell.size() * sizeof(DevShell)),
            i_rad = add(drad.data(), drad.size() * sizeof(DevRadial)),
            i_coef = add(coef.data(), coef.size() * 8), i_coefdd = add(coef_dd.data(), coef_dd.size() * 4),
            i_scoef = add(scoef.data(), scoef.size() * 4),
@@ -694,6 +715,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     P.atom_loc = (const int *)at(i_aloc);
     P.species = (const DevSpecies *)at(i_sp);
     P.shell_rad = (const int *)at(i_shr);
+    P.shells = (const DevShell *)at(i_dsh);
+    P.n_shells = (int)shell_rad.size();
     P.radials = (const DevRadial *)at(i_rad);
     P.coef = (const double *)at(i_coef);
     P.coef_dd = (const float4 *)at(i_coefdd);
@@ -750,7 +773,8 @@ int check_compute(fgi_ctx *c)
 
 size_t workspace_need(fgi_ctx *c)
 {
-    return std::max(c->ws_f64_bytes, std::max(tc_workspace_bytes(c->tc), tc_workspace_bytes(c->tcd)));
+    return std::max(std::max(c->ws_f64_bytes, tc_workspace_bytes(c->tca)),
+                    std::max(tc_workspace_bytes(c->tc), tc_workspace_bytes(c->tcd)));
 }
 
 int check_ws(fgi_ctx *c, void *ws, size_t bytes)
@@ -762,6 +786,15 @@ int check_ws(fgi_ctx *c, void *ws, size_t bytes)
 }
 
 // Launch-profiling scope: events around one launch on the call's stream.
+bool known_precision(int p)
+{
+    return p == FGI_FP64 || p == FGI_SPLIT_BF16 || p == FGI_BF16;
+}
+
+// BF16 terms per operand value on the tensor-core paths: 3 (split BF16, 8
+// products) or 1 (plain BF16)
+int split_terms(int p) { return p == FGI_SPLIT_BF16 ? 3 : 1; }
+
 struct ProfScope {
     fgi_ctx *c;
     cudaStream_t s;
@@ -857,7 +890,7 @@ int internal_integrate_h(fgi_ctx *c, const double *v, double *h, int accumulate,
         }
         return FGI_OK;
     }
-    const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+    const int n_split = split_terms(c->precision);
     DevPlan P = c->dp;
     P.batches = c->tc.d_sb;
     P.act = c->tc.d_sact;
@@ -1023,7 +1056,7 @@ int fgi_plan(fgi_ctx *c, fgi_precision precision, const char *tune_cache_path)
 {
     if (!c) return FGI_ERR_ARG;
     if (!c->have_systems || !c->have_grid) return set_err(c, FGI_ERR_STATE, "set systems and grid before fgi_plan");
-    if (precision != FGI_FP64 && precision != FGI_SPLIT_BF16 && precision != FGI_BF16)
+    if (!known_precision(precision))
         return set_err(c, FGI_ERR_ARG, "unknown precision %d", (int)precision);
     for (int b : c->batch_sys)
         if (b >= c->n_sys) return set_err(c, FGI_ERR_ARG, "grid: batch_sys out of range");
@@ -1050,7 +1083,7 @@ int fgi_set_precision(fgi_ctx *c, fgi_precision precision)
 {
     int rc = check_ready(c);
     if (rc) return rc;
-    if (precision != FGI_FP64 && precision != FGI_SPLIT_BF16 && precision != FGI_BF16)
+    if (!known_precision(precision))
         return set_err(c, FGI_ERR_ARG, "unknown precision %d", (int)precision);
     c->precision = precision;
     return FGI_OK;
@@ -1190,7 +1223,7 @@ int fgi_density(fgi_ctx *c, const double *d, double *n, double *traces, void *ws
                                            nullptr, s));
         }
     } else {
-        const int n_split = c->precision == FGI_SPLIT_BF16 ? 3 : 1;
+        const int n_split = split_terms(c->precision);
         DevPlan Q = c->dp;
         Q.batches = c->tcd.d_sb;
         Q.act = c->tcd.d_sact;
@@ -1232,6 +1265,34 @@ int fgi_adjoint(fgi_ctx *c, const double *gv, const double *v, double *dv, doubl
     CUDA_TRY(c, cudaMemsetAsync(dR, 0, c->atom_species.size() * 3 * sizeof(double), s));
     DevPlan P = c->dp;
     P.batches = c->d_batches_f64;
+    if (c->precision != FGI_FP64) {
+        // tensor-core adjoint on the density's tiles: G gathered in full (its
+        // off-diagonal stored values halved), E = G Phi on tcgen05, dv from
+        // the contraction's epilogue, dR from E and the basis gradients
+        const int n_split = split_terms(c->precision);
+        DevPlan Q = c->dp;
+        Q.batches = c->tca.d_sb;
+        Q.act = c->tca.d_sact;
+        {
+            ProfScope ps(c, s, 4, 0.0, 16.0 * c->nnz, 2);          // conversion of G and its bounds
+            CUDA_TRY(c, tc_launch_to_df(c->tca, Q, gv, ws, c->d_sys_val0, c->d_sys_nnz, c->d_fn_sys, s));
+        }
+        for (const TcWave &w : c->tca.waves) {
+            {
+                ProfScope ps(c, s, 0, w.phi_flops, w.phi_bytes);
+                CUDA_TRY(c, tc_launch_phi_cols(c->tca, Q, w, ws, n_split, s));
+            }
+            {
+                ProfScope ps(c, s, 4, 0.0, 2.0 * w.g_bytes);
+                CUDA_TRY(c, tc_launch_gather_d(c->tca, Q, w, 0.5, ws, n_split, s, true));
+            }
+            // full G: twice the density's upper-block-triangle work, plus the gradient
+            ProfScope ps(c, s, 3, 2.0 * w.n_flops + 40.0 * w.phi_flops / 30.0, w.n_bytes, 3);
+            CUDA_TRY(c, tc_launch_adjoint(c->tca, Q, w, ws, v, dv, dR, n_split, s));
+        }
+        CUDA_TRY(c, launch_scale_by_weight(P, c->n_pts, dv, s));
+        return FGI_OK;
+    }
     size_t max_elems = 0;
     for (const Wave &w : c->waves) max_elems = std::max(max_elems, w.ws_elems);
     double *phi_ws = (double *)ws;

@@ -35,6 +35,18 @@ struct DevSpecies {
     long long scoef_off;  // shared grid: first float4 of the species in scoef
     int nk;               // shared grid: knots
     float inv_h_hi, inv_h_lo;   // shared grid: 1/h as a double-float
+    int lmax;             // largest angular momentum of its shells
+};
+
+// One radial shell of a species (index shell0 + sh), the fields the
+// tensor-core basis kernels read, packed in 32 bytes.
+struct DevShell {
+    int coef_off;         // first interval of the radial in coef_dd (units of 4 coefficients)
+    int nk;               // knots
+    int l;
+    float rcut_f;         // cutoff rounded to FP32
+    float inv_h_hi, inv_h_lo;   // 1/h as a double-float
+    int bound_off;        // first entry of its suffix bounds of |u(r)/r| in DevPlan::rbound
     int pad;
 };
 
@@ -70,6 +82,8 @@ struct DevPlan {
     // basis
     const DevSpecies *species;
     const int *shell_rad;         // radial id per species shell
+    const DevShell *shells;       // the same shells, packed for the tensor-core basis kernels
+    int n_shells;                 // entries of shell_rad / shells
     const DevRadial *radials;
     const double *coef;           // [sum intervals][4] FP64
     const float4 *coef_dd;        // [sum intervals][2]: the four coefficients as double-floats (hi, lo)

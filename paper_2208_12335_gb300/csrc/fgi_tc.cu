@@ -282,24 +282,6 @@ __device__ __forceinline__ void split_fixed(df x, float scale, float unit, __nv_
     c = __float2bfloat16_rn((d - __bfloat162float(b)) + x.lo);
 }
 
-__device__ __forceinline__ void store_fixed8v(uint8_t *dst, long long plane, const df *x, const float *scale,
-                                              const float *unit)
-{
-    uint32_t w0[4], w1[4], w2[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-        split_fixed(x[2 * q], scale[2 * q], unit[2 * q], a0, a1, a2);
-        split_fixed(x[2 * q + 1], scale[2 * q + 1], unit[2 * q + 1], b0, b1, b2);
-        w0[q] = pack_bf16(a0, b0);
-        w1[q] = pack_bf16(a1, b1);
-        w2[q] = pack_bf16(a2, b2);
-    }
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    *reinterpret_cast<uint4 *>(dst + plane) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4 *>(dst + 2 * plane) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-}
-
 __device__ __forceinline__ void store_fixed8(uint8_t *dst, long long plane, const df *x, float scale, float unit)
 {
     uint32_t w0[4], w1[4], w2[4];
@@ -382,13 +364,59 @@ __device__ __forceinline__ const float4 *spline_tab(const DevPlan &P, const DevS
     return P.coef_dd + 2 * R.coef_off;
 }
 
-// The 2l+1 values N_lm u(d)/d^(l+1) Q_lm(x, y, z) of one shell (functions
-// f0 .. f0+2l of the atom; only those in [f_lo, f_hi) are written): the
-// radial factor times each distinct constant in double-float, times the
-// FP32 polynomial.  Unrolled per l so that everything stays in registers.
-template <int L>
-__device__ __forceinline__ void emit_shell(df rad, float x, float y, float z, float2 *out, int f0, int f_lo,
-                                           int f_hi)
+// ----------------------------------------- lane-per-point basis evaluation
+// One lane evaluates every function of one atom at its own point and hands
+// each value straight to an emitter (split + 16-bit stores into the operand
+// image): values never pass through shared memory, and the 32 lanes of a
+// warp (32 consecutive points, one atom) store 64 contiguous bytes of one
+// image row per plane.  The geometry (offset, distance, 1/d^(l+1)) is
+// double-float once per (point, atom); the radial factor once per shell,
+// times the per-point scale of each image; the angular polynomial FP32.
+
+// 16-bit store of the BF16 bits of each plane
+__device__ __forceinline__ void store_bf16x3(uint8_t *dst, long long plane, __nv_bfloat16 a, __nv_bfloat16 b,
+                                             __nv_bfloat16 c)
+{
+    *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(a);
+    *reinterpret_cast<unsigned short *>(dst + plane) = __bfloat16_as_ushort(b);
+    *reinterpret_cast<unsigned short *>(dst + 2 * plane) = __bfloat16_as_ushort(c);
+}
+
+// NSPLIT 3: the fixed-point split on the grid (scale, unit); 1: plain BF16
+template <int NSPLIT>
+__device__ __forceinline__ void store_value(uint8_t *dst, long long plane, df x, float scale, float unit)
+{
+    if (NSPLIT == 3) {
+        __nv_bfloat16 a, b, c;
+        split_fixed(x, scale, unit, a, b, c);
+        store_bf16x3(dst, plane, a, b, c);
+    } else {
+        *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(__float2bfloat16_rn(x.hi));
+    }
+}
+
+// byte offset of element (row r, point p) in the image chunk grid of block I
+// (below 2^31: a batch's image plane is at most 64 blocks x 16 chunks x 16 KB)
+__device__ __forceinline__ int elem_offset(int I, int nc_alloc, int r, int p)
+{
+    const int g = (p >> 3) & 7;
+    return ((I * nc_alloc + (p >> 6)) * 16 + (r >> 3)) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4) + (p & 7) * 2;
+}
+
+__device__ __forceinline__ void store_zero(uint8_t *dst, long long plane, int nsplit)
+{
+    *reinterpret_cast<unsigned short *>(dst) = 0;
+    if (nsplit > 1) {
+        *reinterpret_cast<unsigned short *>(dst + plane) = 0;
+        *reinterpret_cast<unsigned short *>(dst + 2 * plane) = 0;
+    }
+}
+
+// the 2l+1 values of one shell for NIMG radial factors rk[k]
+// (= u/d^(l+1) times the image's per-point scale)
+template <int L, int NIMG, class Emit>
+__device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, float z, int f0, int f_lo, int f_hi,
+                                                Emit &emit)
 {
     constexpr int NM = 2 * L + 1;
     float Q[7];
@@ -396,132 +424,205 @@ __device__ __forceinline__ void emit_shell(df rad, float x, float y, float z, fl
     ylm_poly_f32(L, x, y, z, Q, ci);
     constexpr int NC = L < 2 ? 1 : (L == 2 ? 3 : 5);
     constexpr int C0 = L == 0 ? 0 : (L == 1 ? 1 : (L == 2 ? 2 : 5));
-    df rc[NC];
+    df rc[NIMG][NC];
 #pragma unroll
-    for (int c = 0; c < NC; c++) rc[c] = df_mul(rad, df{kYlmC[C0 + c].x, kYlmC[C0 + c].y});
+    for (int k = 0; k < NIMG; k++)
+#pragma unroll
+        for (int c = 0; c < NC; c++) rc[k][c] = df_mul(rk[k], df{kYlmC[C0 + c].x, kYlmC[C0 + c].y});
+    const bool whole = f0 >= f_lo && f0 + NM <= f_hi;
 #pragma unroll
     for (int m = 0; m < NM; m++) {
         const int fm = f0 + m;
-        if (fm < f_lo || fm >= f_hi) continue;
-        const df val = df_mul_f(rc[ci[m] - C0], Q[m]);
-        out[fm * kPhiValStride] = make_float2(val.hi, val.lo);
+        if (!whole && (fm < f_lo || fm >= f_hi)) continue;
+        df val[NIMG];
+#pragma unroll
+        for (int k = 0; k < NIMG; k++) val[k] = df_mul_f(rc[k][ci[m] - C0], Q[m]);
+        emit(fm, val);
     }
 }
 
-// Double-float phi for rows [r0, r0+128) (atoms e0..e0+ne-1 of the batch)
-// at the 32 points p0..p0+31, into phi_smem[row - r0][point - p0] (zero for
-// points beyond the batch).
-__device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatch &B, const DevAct *act, int e0,
-                                                 int ne, int r0, int p0, float2 *phi_smem)
+// Every function [f_lo, f_hi) of atom `atom` (species S, shell table sh_tab
+// indexed from S.shell0) at the point whose double-float coordinates pp
+// holds (nullptr: no point).  emit(f, val[NIMG]) receives phi times the
+// image's scale (SCALED false: image 0 unscaled); emit0(f) a value that is
+// zero in every image (beyond the species' cutoff, or no point).  The
+// per-point scales are folded into the powers 1/d^(l+1) once per
+// (point, atom).
+template <int NIMG, bool SCALED, class Emit, class Emit0>
+__device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecies &S, const DevShell *sh_tab,
+                                               int atom, const float *pp, int f_lo, int f_hi, const df *scale,
+                                               Emit &emit, Emit0 &emit0)
 {
-    for (int u = threadIdx.x; u < ne * 32; u += blockDim.x) {
-        const int e = e0 + (u >> 5), k = u & 31, p = p0 + k;
-        const DevAct A = act[e];
-        const DevSpecies S = P.species[P.atom_species[A.atom]];
-        const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
-        float2 *out = phi_smem + (A.fn_loc - r0) * kPhiValStride + k;
-        if (p >= B.np) {
-            for (int f = f_lo; f < f_hi; f++) out[f * kPhiValStride] = make_float2(0.f, 0.f);
+    const df zero{0.f, 0.f};
+    bool none = pp == nullptr;
+    const float *aa = P.atom_dd + 6 * atom;
+    if (!none) {
+        // beyond the species' largest cutoff every value is zero (FP32
+        // distance, relative error ~1e-7, against the cutoff with a 1e-5 margin)
+        const float xf = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+        const float yf = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+        const float zf = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+        const float rcs = (float)S.rcut * 1.00001f;
+        none = xf * xf + yf * yf + zf * zf > rcs * rcs;
+    }
+    if (none) {
+        for (int f = f_lo; f < f_hi; f++) emit0(f);
+        return;
+    }
+    const df x = df_sub(df{pp[0], pp[1]}, df{aa[0], aa[1]});
+    const df y = df_sub(df{pp[2], pp[3]}, df{aa[2], aa[3]});
+    const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
+    const df d = df_sqrt(df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z)));
+    const bool origin = d.hi < 1e-12f;
+    // 1/d^(l+1) for l <= lmax, times each image's scale
+    df ip[NIMG][4];
+    {
+        df i0 = origin ? zero : df_rcp(d);
+        df pw[4];
+        pw[0] = i0;
+        pw[1] = S.lmax >= 1 ? df_mul(i0, i0) : zero;
+        pw[2] = S.lmax >= 2 ? df_mul(pw[1], i0) : zero;
+        pw[3] = S.lmax >= 3 ? df_mul(pw[2], i0) : zero;
+#pragma unroll
+        for (int k = 0; k < NIMG; k++) {
+            const bool sc = SCALED || k > 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) ip[k][q] = (sc && q <= S.lmax) ? df_mul(pw[q], scale[k]) : pw[q];
+        }
+    }
+    float grid_hi = -1.f, grid_lo = 0.f, t = 0.f, tl = 0.f;
+    int grid_nk = -1, kk = 0;
+    const float4 *sc = nullptr;
+    if (S.shared_grid && !origin) {
+        const df sd = df_mul(d, df{S.inv_h_hi, S.inv_h_lo});
+        kk = (int)floorf(sd.hi);
+        kk = max(0, min(kk, S.nk - 2));
+        t = sd.hi - (float)kk;
+        tl = sd.lo;
+        sc = P.scoef + S.scoef_off + 2 * ((long long)kk * S.n_shell);
+    }
+    int f = 0;
+    for (int sh = 0; sh < S.n_shell; sh++) {
+        const DevShell R = sh_tab[S.shell0 + sh];
+        const int nm = 2 * R.l + 1;
+        if (f + nm <= f_lo || f >= f_hi) {
+            f += nm;
             continue;
         }
-        const float *pp = P.pts_dd + 6 * (B.pt0 + p);
-        const float *aa = P.atom_dd + 6 * A.atom;
-        {
-            // beyond the largest cutoff of the atom's shells every value is
-            // zero: an FP32 distance (relative error ~1e-7) against the cutoff
-            // with a 1e-5 margin decides, without the double-float work
-            const float xf = (pp[0] - aa[0]) + (pp[1] - aa[1]);
-            const float yf = (pp[2] - aa[2]) + (pp[3] - aa[3]);
-            const float zf = (pp[4] - aa[4]) + (pp[5] - aa[5]);
-            const float rc = (float)S.rcut * 1.00001f;
-            if (xf * xf + yf * yf + zf * zf > rc * rc) {
-                for (int f = f_lo; f < f_hi; f++) out[f * kPhiValStride] = make_float2(0.f, 0.f);
-                continue;
-            }
-        }
-        const df x = df_sub(df{pp[0], pp[1]}, df{aa[0], aa[1]});
-        const df y = df_sub(df{pp[2], pp[3]}, df{aa[2], aa[3]});
-        const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
-        const df d = df_sqrt(df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z)));
-        const bool origin = d.hi < 1e-12f;
-        // 1/d^(l+1), l = 0..3, as double-floats
-        df ipow[4];
-        ipow[0] = origin ? df{0.f, 0.f} : df_rcp(d);
-        ipow[1] = df_mul(ipow[0], ipow[0]);
-        ipow[2] = df_mul(ipow[1], ipow[0]);
-        ipow[3] = df_mul(ipow[2], ipow[0]);
-        int f = 0;
-        // knot interval and offset, shared by consecutive shells on the same
-        // knot grid; t = d/h - k kept as the unevaluated pair t + tl (the
-        // subtraction of the integer part is exact)
-        float grid_hi = -1.f, grid_lo = 0.f, t = 0.f, tl = 0.f;
-        int grid_nk = -1, kk = 0;
-        const float4 *sc = nullptr;            // species on one grid: this point's interval row
-        if (S.shared_grid && !origin) {
-            const df sd = df_mul(d, df{S.inv_h_hi, S.inv_h_lo});
-            kk = (int)floorf(sd.hi);
-            kk = max(0, min(kk, S.nk - 2));
-            t = sd.hi - (float)kk;
-            tl = sd.lo;
-            sc = P.scoef + S.scoef_off + 2 * ((long long)kk * S.n_shell);
-        }
-        for (int sh = 0; sh < S.n_shell; sh++) {
-            const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
-            const int nm = 2 * R.l + 1;
-            if (f + nm <= f_lo || f >= f_hi) {
-                f += nm;
-                continue;
-            }
-            df rad{0.f, 0.f};                      // u(d)/d^(l+1)
-            if (d.hi < R.rcut_f) {
-                if (origin) {
-                    if (R.l == 0) {
-                        const float4 ch = __ldg(P.coef_dd + 2 * R.coef_off), cl = __ldg(P.coef_dd + 2 * R.coef_off + 1);
-                        rad = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});
-                    }
-                } else {
-                    // t = frac(d/h) from the double-float d; u = c0 + t c1 + t^2 (c2 + t c3)
-                    // with c0 + t c1 in double-float and only the t^2 part in FP32: near
-                    // a nucleus u is mostly t c1 (u(0) = 0 for s shells), and an FP32
-                    // t c1 would carry its 2^-24 rounding into the largest densities
-                    const float4 *ce;
-                    if (sc) {
-                        ce = sc + 2 * sh;
-                    } else {
-                        if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
-                            grid_hi = R.inv_h_hi;
-                            grid_lo = R.inv_h_lo;
-                            grid_nk = R.nk;
-                            const df s = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
-                            kk = (int)floorf(s.hi);
-                            kk = max(0, min(kk, R.nk - 2));
-                            t = s.hi - (float)kk;
-                            tl = s.lo;
-                        }
-                        ce = P.coef_dd + 2 * (R.coef_off + kk);
-                    }
-                    const float4 ch = __ldg(ce);
-                    const float4 cl = __ldg(ce + 1);
-                    // t c1 with t = t + tl, c1 = ch.y + cl.y: exact product of the high
-                    // parts plus the two cross terms
-                    const df lin = df_two_prod(t, ch.y);
-                    const float lin_lo = fmaf(t, cl.y, fmaf(tl, ch.y, lin.lo));
-                    const float quad = (t * t) * fmaf(t, ch.w, ch.z);
-                    df uu = df_two_sum(ch.x, lin.hi);
-                    // the t^2 part may exceed c0 + t c1 (p and d shells near a nucleus)
-                    uu = df_two_sum(uu.hi, uu.lo + ((cl.x + lin_lo) + quad));
-                    const df ip = R.l == 0 ? ipow[0] : (R.l == 1 ? ipow[1] : (R.l == 2 ? ipow[2] : ipow[3]));
-                    rad = df_mul(uu, ip);
+        df uu = zero;                                   // u(d), or its limit u'(0) d at the origin
+        bool live = d.hi < R.rcut_f;
+        if (live) {
+            if (origin) {
+                live = R.l == 0;
+                if (live) {
+                    const float4 ch = __ldg(P.coef_dd + 2 * R.coef_off), cl = __ldg(P.coef_dd + 2 * R.coef_off + 1);
+                    uu = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});   // the l = 0 limit c1/h
                 }
+            } else {
+                const float4 *ce;
+                if (sc) {
+                    ce = sc + 2 * sh;
+                } else {
+                    if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
+                        grid_hi = R.inv_h_hi;
+                        grid_lo = R.inv_h_lo;
+                        grid_nk = R.nk;
+                        const df s2 = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
+                        kk = (int)floorf(s2.hi);
+                        kk = max(0, min(kk, R.nk - 2));
+                        t = s2.hi - (float)kk;
+                        tl = s2.lo;
+                    }
+                    ce = P.coef_dd + 2 * (R.coef_off + kk);
+                }
+                // u = c0 + t c1 + t^2 (c2 + t c3): c0 + t c1 in double-float
+                const float4 ch = __ldg(ce);
+                const float4 cl = __ldg(ce + 1);
+                const df lin = df_two_prod(t, ch.y);
+                const float lin_lo = fmaf(t, cl.y, fmaf(tl, ch.y, lin.lo));
+                const float quad = (t * t) * fmaf(t, ch.w, ch.z);
+                uu = df_two_sum(ch.x, lin.hi);
+                uu = df_two_sum(uu.hi, uu.lo + ((cl.x + lin_lo) + quad));
             }
-            switch (R.l) {
-            case 0: emit_shell<0>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
-            case 1: emit_shell<1>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
-            case 2: emit_shell<2>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
-            default: emit_shell<3>(rad, x.hi, y.hi, z.hi, out, f, f_lo, f_hi); break;
-            }
-            f += nm;
         }
+        if (!live) {
+            const int m0 = max(f, f_lo), m1 = min(f + nm, f_hi);
+            for (int m = m0; m < m1; m++) emit0(m);
+            f += nm;
+            continue;
+        }
+        df rk[NIMG];
+        if (origin) {
+#pragma unroll
+            for (int k = 0; k < NIMG; k++) rk[k] = (SCALED || k > 0) ? df_mul(uu, scale[k]) : uu;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NIMG; k++)
+                rk[k] = df_mul(uu, R.l == 0 ? ip[k][0] : (R.l == 1 ? ip[k][1] : (R.l == 2 ? ip[k][2] : ip[k][3])));
+        }
+        switch (R.l) {
+        case 0: emit_shell_lane<0, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
+        case 1: emit_shell_lane<1, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
+        case 2: emit_shell_lane<2, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
+        default: emit_shell_lane<3, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
+        }
+        f += nm;
+    }
+}
+
+// the species' shells for one CTA: shared memory when they fit
+constexpr int kMaxShellsSmem = 64;
+__device__ __forceinline__ const DevShell *stage_shells(const DevPlan &P, DevShell *smem)
+{
+    if (P.n_shells > kMaxShellsSmem) return P.shells;
+    for (int i = threadIdx.x; i < P.n_shells; i += blockDim.x) smem[i] = P.shells[i];
+    return smem;                                    // valid after the caller's next __syncthreads
+}
+
+// H images of one 128-row block: warp tasks (atom of the block, 32-point
+// group), lane = point.  NIMG 1: psi = phi sqrt|w v| on the second grid set;
+// NIMG 2: phi (first set) and w v phi (second set) into two images.
+template <int NIMG, int NSPLIT>
+__device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &B, const TcBatch &T,
+                                              const DevAct *act, const DevShell *sh_tab, int I, int e0, int ne,
+                                              uint8_t *img0, uint8_t *img1, const float2 *wvs,
+                                              const float (*fsc)[128][2])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int r0 = I * 128;
+    const int ng = 2 * T.nc;                       // 32-point groups covering the image's chunks
+    for (int task = warp; task < ne * ng; task += nwarp) {
+        const int eq = task / ng, q = task - eq * ng;
+        const DevAct A = act[e0 + eq];
+        const DevSpecies S = P.species[P.atom_species[A.atom]];
+        const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
+        const int p = q * 32 + lane;
+        const bool live = p < B.np;
+        const float *pp = live ? P.pts_dd + 6 * (B.pt0 + p) : nullptr;
+        df scale[2];
+        const float2 s2 = live ? wvs[p] : make_float2(0.f, 0.f);
+        scale[0] = df{s2.x, s2.y};
+        scale[1] = scale[0];
+        const int rb = A.fn_loc - r0;
+        auto emit = [&](int f, const df *val) {
+            const int r = rb + f;
+            const int off = elem_offset(I, T.nc_alloc, r, p);
+#pragma unroll
+            for (int k = 0; k < NIMG; k++) {
+                const int set = NIMG == 1 ? 1 : k;
+                store_value<NSPLIT>((k == 0 ? img0 : img1) + off, T.plane_phi, val[k], fsc[set][r][0],
+                                    fsc[set][r][1]);
+            }
+        };
+        auto emit0 = [&](int f) {
+            const int off = elem_offset(I, T.nc_alloc, rb + f, p);
+#pragma unroll
+            for (int k = 0; k < NIMG; k++) store_zero((k == 0 ? img0 : img1) + off, T.plane_phi, NSPLIT);
+        };
+        if (NIMG == 1)
+            eval_atom_lane<1, true>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0);
+        else
+            eval_atom_lane<2, false>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0);
     }
 }
 
@@ -540,12 +641,13 @@ __device__ __forceinline__ void eval_block_chunk(const DevPlan &P, const DevBatc
 
 constexpr int kPhiThreads = 256;
 
-__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed,
                                                 int *bsign, int bound)
 {
     extern __shared__ float2 phi_smem[];             // [128][kPhiValStride] double-float values
-    __shared__ float2 wv[32];
+    __shared__ float2 wvs[kMaxBatchPoints];         // per-point image scale (double-float)
+    __shared__ DevShell shs[kMaxShellsSmem];
     __shared__ unsigned int rowmax[2][128];          // |phi|, |w v phi| maxima (float bits)
     __shared__ float rowsum[2][128];                 // sums of |phi|, |w v phi| over the points
     __shared__ float fsc[2][128][2];                 // per row: scale, unit
@@ -562,6 +664,8 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
     const int ne = e1 - e0 + 1;
     uint8_t *phi_img = ws + T.img_phi;
     uint8_t *a_img = ws + T.img_aux;
+    // the species' shells (visible after the barrier below)
+    const DevShell *sh_tab = stage_shells(P, shs);
     // sign of w v over the batch: one sign s (or zero) everywhere lets H use a
     // single image psi = phi sqrt|w v| for both operands, H = s psi^T psi;
     // mixed signs keep the phi and w v phi images
@@ -576,60 +680,73 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
     const int sgn = (pos && neg) ? 0 : (neg ? -1 : 1);
     if (I == 0 && threadIdx.x == 0) bsign[it.batch] = sgn;
     if (fixed && bound) {
-        // row bounds from the tables: per (atom, shell) job and point one
-        // lookup of the suffix bound of |u(r)/r| at the point's distance
-        // (double-float differences, knot index taken from below), times
-        // sqrt|w v| (psi) or |w v| (w v phi) of the point; then max |Y_lm|
-        // per row.  No row sums: the digit width follows the depth alone.
+        // row bounds from the tables: per (atom, shell) and point one lookup
+        // of the suffix bound of |u(r)/r| at the point's distance (knot index
+        // taken from below), times sqrt|w v| (psi) or |w v| (w v phi) of the
+        // point; the maximum over the points times max |Y_lm| bounds each
+        // row, and the same products summed over the points bound the row
+        // sums, so that rows whose sum allows it keep an 8-bit digit.
         for (int q = threadIdx.x; q < 256; q += blockDim.x) {
             (&rowmax[0][0])[q] = 0u;          // rows past n_b stay zero
-            (&rowsum[0][0])[q] = 1.0e30f;
+            (&rowsum[0][0])[q] = 0.f;
         }
         for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
             const float a = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p])) * (1.f + 1.f / 1048576.f);
             wvf[p] = fminf(sgn != 0 ? sqrtf(a) * (1.f + 1.f / 1048576.f) : a, 1.0e30f);
         }
         __syncthreads();
+        // warp tasks (atom of the block, 32-point group), lane = point: the
+        // point's distance once, then per shell one lookup; the warp reduces
+        // each shell's maxima and sums over its 32 points and lane 0 folds
+        // them into the rows (shared-memory atomics across the groups)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-        int job = 0;
-        for (int e = e0; e <= e1; e++) {
-            const DevAct A = act[e];
+        const int ng = (B.np + 31) >> 5;
+        for (int task = warp; task < ne * ng; task += nwarp) {
+            const int eq = task / ng, q = task - eq * ng;
+            const DevAct A = act[e0 + eq];
             const DevSpecies S = P.species[P.atom_species[A.atom]];
             const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
-            const float *aa = P.atom_dd + 6 * A.atom;
+            const int p = q * 32 + lane;
+            float d = 3.0e38f, wp = 0.f;
+            if (p < B.np) {
+                const float *aa = P.atom_dd + 6 * A.atom;
+                const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+                const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+                const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+                const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+                d = sqrtf(x * x + y * y + z * z);
+                wp = wvf[p];
+            }
             int f = 0;
             for (int sh = 0; sh < S.n_shell; sh++) {
-                const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                const DevShell R = sh_tab[S.shell0 + sh];
                 const int nm = 2 * R.l + 1;
                 const int f1 = f;
                 f += nm;
                 if (f <= f_lo || f1 >= f_hi) continue;
-                if ((job++ % nwarp) != warp) continue;
-                const float *tabr = P.rbound + R.bound_off;
-                float m0 = 0.f, m1 = 0.f;
-                for (int p = lane; p < B.np; p += 32) {
-                    const float *pp = P.pts_dd + 6 * (B.pt0 + p);
-                    const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
-                    const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
-                    const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
-                    const float d = sqrtf(x * x + y * y + z * z);
-                    if (d >= R.rcut_f * 1.00001f) continue;
+                float t = 0.f;
+                if (d < R.rcut_f * 1.00001f) {
                     const int ki = min(max((int)(d * 0.999999f * R.inv_h_hi), 0), R.nk - 2);
-                    const float t = __ldg(tabr + ki);
-                    m0 = fmaxf(m0, t);
-                    m1 = fmaxf(m1, t * wvf[p]);
+                    t = __ldg(P.rbound + R.bound_off + ki);
                 }
-                m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
-                m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
-                if (lane == 0) {
-                    for (int m = 0; m < nm; m++) {
-                        const int fr = f1 + m;
-                        if (fr < f_lo || fr >= f_hi) continue;
-                        const int row = A.fn_loc + fr - r0;
-                        const float yl = __ldg(P.rbound + R.l * R.l + m);
-                        rowmax[0][row] = __float_as_uint(fminf(m0 * yl, 1.0e30f));
-                        rowmax[1][row] = __float_as_uint(fminf(m1 * yl, 1.0e30f));
-                    }
+                const float tw = t * wp;
+                const float m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(t)));
+                const float m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(tw)));
+                float s0 = t, s1 = tw;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                }
+                // lane m folds function m of the shell into its row
+                const int fr = f1 + lane;
+                if (lane < nm && m0 > 0.f && fr >= f_lo && fr < f_hi) {
+                    const int row = A.fn_loc + fr - r0;
+                    const float yl = __ldg(P.rbound + R.l * R.l + lane);
+                    atomicMax(&rowmax[0][row], __float_as_uint(fminf(m0 * yl, 1.0e30f)));
+                    atomicMax(&rowmax[1][row], __float_as_uint(fminf(m1 * yl, 1.0e30f)));
+                    atomicAdd(&rowsum[0][row], fminf(s0 * 1.0001f * yl, 1.0e30f));   // 1.0001: FP32 sums
+                    atomicAdd(&rowsum[1][row], fminf(s1 * 1.0001f * yl, 1.0e30f));
                 }
             }
         }
@@ -757,51 +874,34 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
         }
         __syncthreads();
     }
-    for (int c2 = 0; c2 < 2 * T.nc; c2++) {
-        const int c = c2 >> 1, half = c2 & 1;
-        eval_block_chunk(P, B, act, e0, ne, r0, c * 64 + half * 32, phi_smem);
-        if (threadIdx.x < 32) {
-            const int p = c * 64 + half * 32 + threadIdx.x;
-            double s = 0.0;
-            if (v && p < B.np) {
-                const double vv = v[B.pt0 + p];
-                if (!isfinite(vv)) atomicOr(P.status, kStatusNonFinite);
-                s = P.pw[B.pt0 + p] * vv;
-            }
-            df sd = df_from_double(sgn != 0 ? fabs(s) : s);
-            if (sgn != 0) sd = df_sqrt(sd);                 // sqrt|w v| for psi
-            wv[threadIdx.x] = make_float2(sd.hi, sd.lo);
+    // the per-point scale of the images: sqrt|w v| (psi) or w v (mixed signs)
+    for (int p = threadIdx.x; p < B.np; p += blockDim.x) {
+        const double vv = v ? v[B.pt0 + p] : 0.0;
+        if (!isfinite(vv)) atomicOr(P.status, kStatusNonFinite);
+        const double s = P.pw[B.pt0 + p] * vv;
+        df sd = df_from_double(sgn != 0 ? fabs(s) : s);
+        if (sgn != 0) sd = df_sqrt(sd);
+        wvs[p] = make_float2(sd.hi, sd.lo);
+    }
+    __syncthreads();
+    uint8_t *img1 = sgn == 0 ? a_img : phi_img;
+    if (sgn != 0) {
+        if (fixed) h_image_lanes<1, 3>(P, B, T, act, sh_tab, I, e0, ne, phi_img, img1, wvs, fsc);
+        else h_image_lanes<1, 1>(P, B, T, act, sh_tab, I, e0, ne, phi_img, img1, wvs, fsc);
+    } else {
+        if (fixed) h_image_lanes<2, 3>(P, B, T, act, sh_tab, I, e0, ne, phi_img, img1, wvs, fsc);
+        else h_image_lanes<2, 1>(P, B, T, act, sh_tab, I, e0, ne, phi_img, img1, wvs, fsc);
+    }
+    // rows past n_b in the last block: zeros (whole 16-byte units)
+    const int nlive = rend - r0;
+    const int nplanes = fixed ? 3 : 1;
+    for (int u = threadIdx.x; u < (128 - nlive) * T.nc * 8; u += blockDim.x) {
+        const int r = nlive + u / (T.nc * 8), cg = u % (T.nc * 8);
+        const long long off = unit_offset(I, T.nc_alloc, cg >> 3, r, cg & 7);
+        for (int pl = 0; pl < nplanes; pl++) {
+            *reinterpret_cast<uint4 *>(phi_img + off + pl * T.plane_phi) = make_uint4(0u, 0u, 0u, 0u);
+            if (sgn == 0) *reinterpret_cast<uint4 *>(a_img + off + pl * T.plane_phi) = make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        for (int u = threadIdx.x; u < 512; u += blockDim.x) {
-            const int r = u >> 2, gg = u & 3, g = half * 4 + gg;
-            const bool live = r0 + r < B.nfn;
-            df x[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const float2 t = live ? phi_smem[r * kPhiValStride + gg * 8 + q] : make_float2(0.f, 0.f);
-                x[q] = df{t.x, t.y};
-            }
-            const long long off = unit_offset(I, T.nc_alloc, c, r, g);
-            if (sgn == 0) {
-                if (fixed)
-                    store_fixed8(phi_img + off, T.plane_phi, x, fsc[0][r][0], fsc[0][r][1]);
-                else
-                    store_split8_df(phi_img + off, T.plane_phi, x, n_split);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const float2 s = wv[gg * 8 + q];
-                x[q] = df_mul(x[q], df{s.x, s.y});
-            }
-            // w v phi (mixed signs) or psi = phi sqrt|w v| (into the phi image)
-            uint8_t *dst = (sgn == 0 ? a_img : phi_img) + off;
-            if (fixed)
-                store_fixed8(dst, T.plane_phi, x, fsc[1][r][0], fsc[1][r][1]);
-            else
-                store_split8_df(dst, T.plane_phi, x, n_split);
-        }
-        __syncthreads();
     }
 }
 
@@ -809,14 +909,14 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
 // density contracts over functions, so the fixed-point grid of the leading
 // term is per point (column): first the largest |phi_i(p)| over all of the
 // batch's functions (FP32), then every 128-row block in double-float.
-__global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                      uint8_t *ws, int n_split, int bound)
 {
-    extern __shared__ float2 phi_smem[];
     __shared__ unsigned int colmax[64];
     __shared__ float colsum[64];
     __shared__ float csc[2][64];
     __shared__ float ymax[kMaxL + 1];                // max over m of max |Y_lm|, per l
+    __shared__ DevShell shs[kMaxShellsSmem];
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
     const TcBatch T = tb[it.batch];
@@ -824,6 +924,8 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
     const DevAct *act = P.act + B.act0;
     uint8_t *phi_img = ws + T.img_phi;
     const bool fixed = n_split == 3;
+    const DevShell *sh_tab = stage_shells(P, shs);
+    __syncthreads();
     if (fixed) {
         if (threadIdx.x < 64) {
             colmax[threadIdx.x] = 0u;
@@ -854,7 +956,7 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
                 // from below against FP32 rounding of d
                 const float dl = d * 0.999999f;
                 for (int sh = 0; sh < S.n_shell; sh++) {
-                    const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                    const DevShell R = sh_tab[S.shell0 + sh];
                     if (d >= R.rcut_f * 1.00001f) continue;
                     const int ki = min(max((int)(dl * R.inv_h_hi), 0), R.nk - 2);
                     const float tb = __ldg(P.rbound + R.bound_off + ki);
@@ -899,30 +1001,37 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
         }
         __syncthreads();
     }
-    for (int I2 = 0; I2 < 2 * T.nrb; I2++) {
-        const int I = I2 >> 1, half = I2 & 1;
-        const int r0 = I * 128;
-        const int rend = min(r0 + 128, B.nfn);
-        const int e0 = find_act(act, B.n_act, r0);
-        const int e1 = find_act(act, B.n_act, rend - 1);
-        eval_block_chunk(P, B, act, e0, e1 - e0 + 1, r0, c * 64 + half * 32, phi_smem);
-        __syncthreads();
-        for (int u = threadIdx.x; u < 512; u += blockDim.x) {
-            const int r = u >> 2, gg = u & 3, g = half * 4 + gg;
-            const bool live = r0 + r < B.nfn;
-            df x[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const float2 t = live ? phi_smem[r * kPhiValStride + gg * 8 + q] : make_float2(0.f, 0.f);
-                x[q] = df{t.x, t.y};
-            }
-            const long long off = unit_offset(I, T.nc_alloc, c, r, g);
+    // warp tasks (active atom, 32-point half of the chunk), lane = point:
+    // every function of the atom at the lane's point, split on the point's grid
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int nsplit = fixed ? 3 : 1;
+    for (int task = warp; task < B.n_act * 2; task += nwarp) {
+        const DevAct A = act[task >> 1];
+        const DevSpecies S = P.species[P.atom_species[A.atom]];
+        const int k = (task & 1) * 32 + lane, p = c * 64 + k;
+        const float *pp = p < B.np ? P.pts_dd + 6 * (B.pt0 + p) : nullptr;
+        const float sc = fixed ? csc[0][k] : 0.f, un = fixed ? csc[1][k] : 0.f;
+        auto emit = [&](int f, const df *val) {
+            const int rg = A.fn_loc + f;
+            const int off = elem_offset(rg >> 7, T.nc_alloc, rg & 127, p);
             if (fixed)
-                store_fixed8v(phi_img + off, T.plane_phi, x, &csc[0][g * 8], &csc[1][g * 8]);
+                store_value<3>(phi_img + off, T.plane_phi, val[0], sc, un);
             else
-                store_split8_df(phi_img + off, T.plane_phi, x, n_split);
-        }
-        __syncthreads();
+                store_value<1>(phi_img + off, T.plane_phi, val[0], sc, un);
+        };
+        auto emit0 = [&](int f) {
+            const int rg = A.fn_loc + f;
+            store_zero(phi_img + elem_offset(rg >> 7, T.nc_alloc, rg & 127, p), T.plane_phi, nsplit);
+        };
+        eval_atom_lane<1, false>(P, S, sh_tab, A.atom, pp, 0, S.n_fn, nullptr, emit, emit0);
+    }
+    // rows [n_b, 64 nkc) of the contraction's last function chunk: zeros
+    const int nplanes = fixed ? 3 : 1;
+    for (int u = threadIdx.x; u < (T.nkc * 64 - B.nfn) * 8; u += blockDim.x) {
+        const int rg = B.nfn + (u >> 3), g = u & 7;
+        const long long off = unit_offset(rg >> 7, T.nc_alloc, c, rg & 127, g);
+        for (int pl = 0; pl < nplanes; pl++)
+            *reinterpret_cast<uint4 *>(phi_img + off + pl * T.plane_phi) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -1318,7 +1427,7 @@ __global__ void k_d_colbounds(const float2 *v, const int *col_of, long long nnz,
 
 __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                      uint8_t *ws, const float2 *ddv, const unsigned int *gmax,
-                                                     const float *gsum, float offdiag_scale, int n_split)
+                                                     const float *gsum, float offdiag_scale, int n_split, int full)
 {
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
@@ -1343,9 +1452,10 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
     }
     uint8_t *img = ws + T.img_aux;
     // D is symmetric: block row J holds only the chunks i >= 128 J, the
-    // diagonal block halved (n = 2 sum_J phi_J . E_J, exact in binary)
-    for (int kc = 2 * J; kc < T.nkc; kc++) {
-        const float blk = kc < 2 * J + 2 ? 0.5f : 1.f;
+    // diagonal block halved (n = 2 sum_J phi_J . E_J, exact in binary); in
+    // full (the adjoint's G Phi) every chunk, nothing halved
+    for (int kc = full ? 0 : 2 * J; kc < T.nkc; kc++) {
+        const float blk = (!full && kc < 2 * J + 2) ? 0.5f : 1.f;
         __syncthreads();
         if (threadIdx.x < 64) {
             const int i = kc * 64 + threadIdx.x;
@@ -1415,9 +1525,14 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
 // doubles per item.  Many items per batch keep the CTAs on few batches at a
 // time, so the D and phi images are read from L2.  k_density_sum then forms
 // n_p = 2 sum_J partial_J(p).
+//
+// ADJ (the adjoint's E = G Phi): every function chunk of the full G image,
+// and each lane also stores its row of E (acc0 + acc1 in FP32) for the
+// position gradient.
+template <bool ADJ>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                               int n_items, const uint8_t *ws, double *part,
-                                                              int n_split)
+                                                              int n_split, uint8_t *ws_e)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
@@ -1444,7 +1559,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                 const TcBatch T = tb[it.batch];
                 const int m = it.ti, J = it.tj;
                 const uint8_t *d_img = ws + T.img_aux, *phi_img = ws + T.img_phi;
-                for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
+                for (int kc = ADJ ? 0 : 2 * J; kc < T.nkc; kc++, n++) {
                     const int st = (int)(n % kStages);
                     const long long use = n / kStages;
                     if (use > 0 && !mbar_wait_a(&S->empty[st], (uint32_t)((use - 1) & 1), P.status, &S->abort)) {
@@ -1486,7 +1601,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     break;
                 }
                 tc_fence_after();
-                for (int kc = 2 * J; kc < T.nkc; kc++, n++) {
+                const int kc0 = ADJ ? 0 : 2 * J;
+                for (int kc = kc0; kc < T.nkc; kc++, n++) {
                     const int st = (int)(n % kStages);
                     if (!mbar_wait_a(&S->full[st], (uint32_t)((n / kStages) & 1), P.status, &S->abort)) {
                         ok = false;
@@ -1496,9 +1612,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                     const uint8_t *a_sm = sm + st * kStageBytes;
                     if (n_split == 3)
                         mma_chunk<3, kDensityOrder, true>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc,
-                                                          kc == 2 * J);
+                                                          kc == kc0);
                     else
-                        mma_chunk<1, 0, true>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, kc == 2 * J);
+                        mma_chunk<1, 0, true>(tmem + buf * 256, a_sm, a_sm + 3 * kChunkBytes, idesc, kc == kc0);
                     tc_commit(&S->empty[st]);
                 }
                 tc_commit(&S->tfull[buf]);
@@ -1556,6 +1672,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
                 // double-float (FP32 pipe): e = acc0 + acc1, phi = sum of its planes
                 const int c = 2 * m + (cc >> 1);
                 const bool live = ok && j < B.nfn;
+                if (ADJ && live) {
+                    // this lane's row of E at the chunk's 32 points, for the gradient
+                    float4 *dst = reinterpret_cast<float4 *>(ws_e + T.img_e) +
+                                  ((long long)j * T.nc_alloc * 64 + m * 128 + cc * 32) / 4;
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; q4++)
+                        dst[q4] = make_float4(a0[4 * q4] + a1[4 * q4], a0[4 * q4 + 1] + a1[4 * q4 + 1],
+                                              a0[4 * q4 + 2] + a1[4 * q4 + 2], a0[4 * q4 + 3] + a1[4 * q4 + 3]);
+                }
 #pragma unroll
                 for (int gg = 0; gg < 4; gg++) {
                     const int g = (cc & 1) * 4 + gg;
@@ -1620,7 +1745,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_density(DevPlan P, const T
 // n_p = 2 sum_J part[J][p] over the batch's function blocks, in J order
 // (deterministic); one CTA of 128 threads per (batch, point tile).
 __global__ void __launch_bounds__(128) k_density_sum(DevPlan P, const TcBatch *tb, const WorkItem *items,
-                                                    const double *part, double *n_out)
+                                                    const double *part, double *n_out, double factor)
 {
     const WorkItem it = items[blockIdx.x];
     const DevBatch B = P.batches[it.batch];
@@ -1630,7 +1755,105 @@ __global__ void __launch_bounds__(128) k_density_sum(DevPlan P, const TcBatch *t
     const long long nt = T.nc_alloc / 2;
     double s = 0.0;
     for (int J = 0; J < T.nrb; J++) s += part[(T.part0 + J * nt + it.ti) * 128 + threadIdx.x];
-    n_out[B.pt0 + p] = 2.0 * s;
+    n_out[B.pt0 + p] = factor * s;
+}
+
+// sum over the shell's 2l+1 functions of E_i grad phi_i (FP32), unrolled per l
+template <int L>
+__device__ __forceinline__ void adj_shell(float g, float gp, float x, float y, float z, float nx, float ny, float nz,
+                                          const float *Erow, long long Pa, float &gx, float &gy, float &gz)
+{
+    float Y[2 * L + 1], G[2 * L + 1][3];
+    ylm_unit<float>(L, x, y, z, Y);                      // P(r) = r^l Y_lm
+    ylm_poly_grad<float>(L, x, y, z, G);
+#pragma unroll
+    for (int m = 0; m < 2 * L + 1; m++) {
+        const float e = __ldg(Erow + m * Pa);
+        const float a = gp * Y[m];
+        gx = fmaf(e, fmaf(a, nx, g * G[m][0]), gx);
+        gy = fmaf(e, fmaf(a, ny, g * G[m][1]), gy);
+        gz = fmaf(e, fmaf(a, nz, g * G[m][2]), gz);
+    }
+}
+
+// Position gradient of the adjoint on CUDA cores (FP32): CTA per (batch,
+// 64-point chunk); warp tasks (active atom, 32-point half), lane = point.
+// The lane forms sum_{i on the atom} grad phi_i(p) . E_i(p) from the E rows
+// the contraction stored, times -2 w_p v_p; the warp sums its 32 points and
+// adds the atom's three components to dR (FP64 atomics).
+//   grad phi = g'(d) (r/d) P(r) + g(d) grad P(r),  g = u/d^(l+1),
+//   g' = u'/d^(l+1) - (l+1) u/d^(l+2),  P = r^l Y_lm (a polynomial in x, y, z)
+__global__ void __launch_bounds__(256) k_tc_adj_grad(DevPlan P, const TcBatch *tb, const WorkItem *items,
+                                                     const uint8_t *ws, const double *v, double *dR)
+{
+    const WorkItem it = items[blockIdx.x];
+    const DevBatch B = P.batches[it.batch];
+    const TcBatch T = tb[it.batch];
+    const int c = it.ti;
+    const DevAct *act = P.act + B.act0;
+    const float *E = reinterpret_cast<const float *>(ws + T.img_e);
+    const long long Pa = (long long)T.nc_alloc * 64;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int task = warp; task < B.n_act * 2; task += nwarp) {
+        const DevAct A = act[task >> 1];
+        const int p = c * 64 + (task & 1) * 32 + lane;
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        if (p < B.np) {
+            const DevSpecies S = P.species[P.atom_species[A.atom]];
+            const float *pp = P.pts_dd + 6 * (B.pt0 + p);
+            const float *aa = P.atom_dd + 6 * A.atom;
+            const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+            const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+            const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+            const float d = sqrtf(x * x + y * y + z * z);
+            if (d > 1e-12f && d < (float)S.rcut * 1.00001f) {
+                const float inv = 1.f / d;
+                const float nx = x * inv, ny = y * inv, nz = z * inv;
+                int f = 0;
+                for (int sh = 0; sh < S.n_shell; sh++) {
+                    const DevRadial R = P.radials[P.shell_rad[S.shell0 + sh]];
+                    const int nm = 2 * R.l + 1;
+                    if (d >= R.rcut_f) {
+                        f += nm;
+                        continue;
+                    }
+                    const float s = d * R.inv_h_hi;
+                    const int k = min((int)s, R.nk - 2);
+                    const float t = s - (float)k;
+                    const float4 ch = __ldg(P.coef_dd + 2 * (R.coef_off + k));
+                    const float u = ch.x + t * (ch.y + t * (ch.z + t * ch.w));
+                    const float du = (ch.y + t * (2.f * ch.z + 3.f * t * ch.w)) * R.inv_h_hi;
+                    float ipl = inv;
+                    for (int q = 0; q < R.l; q++) ipl *= inv;          // 1/d^(l+1)
+                    const float g = u * ipl;
+                    const float gp = (du - (float)(R.l + 1) * u * inv) * ipl;
+                    const float *Erow = E + (long long)(A.fn_loc + f) * Pa + p;
+                    switch (R.l) {
+                    case 0: adj_shell<0>(g, gp, x, y, z, nx, ny, nz, Erow, Pa, gx, gy, gz); break;
+                    case 1: adj_shell<1>(g, gp, x, y, z, nx, ny, nz, Erow, Pa, gx, gy, gz); break;
+                    case 2: adj_shell<2>(g, gp, x, y, z, nx, ny, nz, Erow, Pa, gx, gy, gz); break;
+                    default: adj_shell<3>(g, gp, x, y, z, nx, ny, nz, Erow, Pa, gx, gy, gz); break;
+                    }
+                    f += nm;
+                }
+                const float pref = (float)(-2.0 * P.pw[B.pt0 + p] * v[B.pt0 + p]);
+                gx *= pref;
+                gy *= pref;
+                gz *= pref;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        }
+        if (lane == 0 && (gx != 0.f || gy != 0.f || gz != 0.f)) {
+            atomicAdd(dR + 3 * A.atom + 0, (double)gx);
+            atomicAdd(dR + 3 * A.atom + 1, (double)gy);
+            atomicAdd(dR + 3 * A.atom + 2, (double)gz);
+        }
+    }
 }
 
 // Dynamic shared memory of the tcgen05 kernels: the two-stage ring (about
@@ -1652,11 +1875,11 @@ cudaError_t set_attrs()
     if (attrs_set) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_tc_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc_h());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
+    e = cudaFuncSetAttribute(k_tc_density<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_density<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc(3));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tc_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_phi_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phi());
     if (e != cudaSuccess) return e;
     attrs_set = true;
     return cudaSuccess;
@@ -1749,6 +1972,8 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         T.plane_phi = (long long)T.nrb * T.nc_alloc * kChunkBytes;
         T.plane_d = (long long)T.nrb * T.nkc * kChunkBytes;
         foot[b] = 3 * (size_t)T.plane_phi + 3 * (size_t)std::max(T.plane_phi, T.plane_d);
+        T.img_e = -1;
+        if (in.with_e) foot[b] += 2 * (size_t)T.plane_phi;     // E in FP32: twice a BF16 plane
     }
     t.bound_grids = in.bound_grids;
     size_t max_ws = 0;
@@ -1781,6 +2006,7 @@ int tc_build(TcPlan &t, const TcPlanInput &in, std::string *err)
         TcBatch &T = t.batches[b];
         T.img_phi = (long long)off;
         T.img_aux = (long long)(off + 3 * (size_t)T.plane_phi);
+        if (in.with_e) T.img_e = (long long)(off + 3 * (size_t)T.plane_phi + 3 * (size_t)std::max(T.plane_phi, T.plane_d));
         T.part0 = part;
         part += part_rows(b);
         off += foot[b];
@@ -1920,7 +2146,7 @@ cudaError_t tc_launch_phi_cols(const TcPlan &t, const DevPlan &P, const TcWave &
                                cudaStream_t s)
 {
     if (w.npc <= 0) return cudaSuccess;
-    k_tc_phi_cols<<<(unsigned)w.npc, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.pc0,
+    k_tc_phi_cols<<<(unsigned)w.npc, kPhiThreads, 0, s>>>(P, t.d_batches, t.d_items + w.pc0,
                                                            (uint8_t *)ws + t.img_base, n_split,
                                                            t.bound_grids >= 1 ? 1 : 0);
     return cudaGetLastError();
@@ -1947,14 +2173,14 @@ cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long 
 }
 
 cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, double offdiag_scale,
-                               void *ws, int n_split, cudaStream_t s)
+                               void *ws, int n_split, cudaStream_t s, bool full)
 {
     if (w.ng <= 0) return cudaSuccess;
     const char *base = (const char *)ws;
     k_tc_gather_d<<<(unsigned)w.ng, 256, 0, s>>>(P, t.d_batches, t.d_items + w.g0, (uint8_t *)ws + t.img_base,
                                                  (const float2 *)base, (const unsigned int *)(base + t.bound_off),
                                                  (const float *)(base + t.bound_off + 4 * t.n_fn),
-                                                 (float)offdiag_scale, n_split);
+                                                 (float)offdiag_scale, n_split, full ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1980,11 +2206,31 @@ cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w
     if (w.nd <= 0) return cudaSuccess;
     double *part = reinterpret_cast<double *>((uint8_t *)const_cast<void *>(ws) + t.img_base + w.part_off);
     const int grid = (int)std::min<long long>(w.ne, t.num_sms);
-    k_tc_density<<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.e0, (int)w.ne,
-                                                      (const uint8_t *)ws + t.img_base, part, n_split);
+    k_tc_density<false><<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.e0, (int)w.ne,
+                                                             (const uint8_t *)ws + t.img_base, part, n_split,
+                                                             nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_density_sum<<<(unsigned)w.nd, 128, 0, s>>>(P, t.d_batches, t.d_items + w.d0, part, n);
+    k_density_sum<<<(unsigned)w.nd, 128, 0, s>>>(P, t.d_batches, t.d_items + w.d0, part, n, 2.0);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adjoint(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, const double *v,
+                              double *dv, double *dR, int n_split, cudaStream_t s)
+{
+    if (w.nd <= 0) return cudaSuccess;
+    if (!t.batches.empty() && t.batches[w.b0].img_e < 0) return cudaErrorInvalidValue;   // no room for E
+    uint8_t *img = (uint8_t *)const_cast<void *>(ws) + t.img_base;
+    double *part = reinterpret_cast<double *>(img + w.part_off);
+    const int grid = (int)std::min<long long>(w.ne, t.num_sms);
+    k_tc_density<true><<<grid, kThreadsTc, smem_tc(3), s>>>(P, t.d_batches, t.d_items + w.e0, (int)w.ne, img, part,
+                                                            n_split, img);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_density_sum<<<(unsigned)w.nd, 128, 0, s>>>(P, t.d_batches, t.d_items + w.d0, part, dv, 1.0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_tc_adj_grad<<<(unsigned)w.npc, 256, 0, s>>>(P, t.d_batches, t.d_items + w.pc0, img, v, dR);
     return cudaGetLastError();
 }
 

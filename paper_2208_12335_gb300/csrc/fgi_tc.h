@@ -28,6 +28,8 @@ struct TcBatch {
     int nc_alloc;          // allocated 64-point chunks (even)
     int nkc;               // 64-function chunks (density contraction depth)
     long long part0;       // first partial-density row of the batch in its wave (128 doubles each)
+    long long img_e;       // byte offset of E = G Phi (FP32 [row][point], rows of 64 nc_alloc points)
+                           // for the adjoint, -1 when the plan keeps no room for it
 };
 
 struct TcWave {
@@ -56,6 +58,7 @@ struct TcPlanInput {
     bool host_only = false;              // build host tables only (no device copies)
     long long wave_mb = 0;               // operand images per wave, MiB (0: default)
     int bound_grids = 0;                 // leading-digit grids from table bounds: 1 density, 2 also H
+    bool with_e = false;                 // room for E = G Phi per batch (the adjoint's tiles)
 };
 
 struct TcPlan {
@@ -101,9 +104,14 @@ cudaError_t tc_launch_fix_to_h(const TcPlan &t, const void *ws, double *h, long 
 cudaError_t tc_launch_to_df(const TcPlan &t, const DevPlan &P, const double *x, void *ws, const long long *sys_val0,
                             const long long *sys_nnz, const int *fn_sys, cudaStream_t s);
 cudaError_t tc_launch_gather_d(const TcPlan &t, const DevPlan &P, const TcWave &w, double offdiag_scale,
-                               void *ws, int n_split, cudaStream_t s);
+                               void *ws, int n_split, cudaStream_t s, bool full = false);
 cudaError_t tc_launch_density(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws,
                               double *n, int n_split, cudaStream_t s);
+// adjoint of one wave (images and G gathered in full as above): E = G Phi on
+// tcgen05 over every function block, dv_p = sum_j phi_j E_j (unweighted) into
+// dv, E kept as FP32, then dR_a += -2 sum_p w_p v_p sum_{i on a} grad phi_i . E_i
+cudaError_t tc_launch_adjoint(const TcPlan &t, const DevPlan &P, const TcWave &w, const void *ws, const double *v,
+                              double *dv, double *dR, int n_split, cudaStream_t s);
 
 // failure-path self-test: a bounded wait that runs out (status time-out)
 cudaError_t tc_launch_wait_selftest(int *status, cudaStream_t s);

@@ -1,9 +1,9 @@
-"""GPU parity of the split path with leading-digit grids taken from table
-bounds of |phi| instead of a pass over the points (tune-file key
-bound_grids: 1 the density images, 2 the H images too): H and density
-against the FP64 oracle on water, a Si64 sub-grid and a sample of the
-1000-atom C/H/N/O cluster, at the split tolerances.  Marked slow
-(collected last)."""
+"""GPU parity of the split path for every setting of the leading-digit
+grids (tune-file key bound_grids): 0 an FP32 pass over the points for the
+H and the density images, 1 table bounds of |phi| for the density images
+only, 2 (the default) table bounds for both: H and density against the
+FP64 oracle on water, a Si64 sub-grid and a sample of the 1000-atom
+C/H/N/O cluster, at the split tolerances.  Marked slow (collected last)."""
 import functools
 
 import numpy as np
@@ -57,7 +57,7 @@ def on_pattern(ctx, n_fn, act, M):
     return out
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name", ["water", "si64", "chno"])
 def test_table_bound_grids_keep_split_parity(fgi, tmp_path, name, mode):
     prob = problem(name)
