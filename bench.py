@@ -366,6 +366,7 @@ def main():
     t0 = time.perf_counter()
     prob, desc = make_workload(args.workload, accel="cuda")
     gen_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()             # the generator's cached device blocks go back
     if args.batches:
         ids = np.sort(np.random.default_rng(99).choice(prob.n_batch, size=min(args.batches, prob.n_batch),
                                                         replace=False))
@@ -768,7 +769,12 @@ def main():
                "fp64_per_molecule_loop": fp64_loop,
                "errors_vs_oracle": errors,
                "clocks": clk.summary(),
-               "profile_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof} if prof else None}
+               "profile_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof} if prof else None,
+               # per step and kernel class: launches and algorithmic FLOPs (the units
+               # the roofline and the DRAM-traffic scaling use)
+               "profile_per_step": ({k: {"launches": prof[k]["launches"] / args.steps,
+                                         "algorithmic_flops": prof[k]["flops"] / args.steps}
+                                     for k in prof} if prof else None)}
         if fp64:
             out["speedup_vs_fp64_gpu"] = fp64["ms_per_step"] / ms_max
         if args.precision != "fp64":

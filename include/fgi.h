@@ -125,12 +125,13 @@ int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w
    super-batch, 0..1024; 0 keeps the given batches), density_sb_growth (limit
    on a super-batch's active functions relative to its largest member,
    1..16), wave_mb (operand-image workspace per wave, MiB), h_sb_points and
-   h_sb_growth (the same two limits for the H path; defaults 400 points and
-   1.25, so only small neighbouring batches merge), bound_grids (0, 1 or 2,
-   default 0: the split images' leading-digit grids from table bounds of
-   |phi| -- max |Y_lm| and per-interval suffix bounds of |u(r)/r| --
-   instead of an FP32 pass over the points, 1 for the density images, 2 for
-   the H images too; it applies only when every radial has u(0) = 0).  A missing file
+   h_sb_growth (the same two limits for the H path; defaults 512 points and
+   1.25: deeper H contractions accumulate more FP32 truncation in the
+   remainder products), bound_grids (0, 1 or 2, default 2: the split images'
+   leading-digit grids from table bounds of |phi| -- max |Y_lm| and
+   per-interval suffix bounds of |u(r)/r| -- for the density images (1) and
+   the H images too (2), instead of an FP32 pass over the points (0); the
+   bounds apply only when every radial has u(0) = 0).  A missing file
    means the defaults; a malformed or out-of-range value is FGI_ERR_ARG.
    For experiments, the environment variables FGI_SB_POINTS,
    FGI_SB_GROWTH, FGI_H_SB_POINTS, FGI_H_SB_GROWTH, FGI_BOUND_GRIDS and FGI_TC_WAVE_MB

@@ -222,7 +222,10 @@ struct TuneSettings {
     int sb_points = 1024;
     double sb_growth = 1.35;
     long long wave_mb = 0;      // 0: the library default
-    int h_sb_points = 400;      // merges small neighbouring batches; no deeper K than the largest batches
+    // merges neighbouring batches (fewer tiles and scatter atomics); 512
+    // points keep the FP32 accumulation of the remainder products (one
+    // truncation per 16-point MMA step) within the H tolerance
+    int h_sb_points = 512;
     double h_sb_growth = 1.25;
     int bound_grids = 2;        // table-bound digit grids for the H and density images
 };

@@ -641,7 +641,7 @@ __device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &
 
 constexpr int kPhiThreads = 256;
 
-__global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed,
                                                 int *bsign, int bound)
 {
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(kPhiThreads, 3) k_tc_phi(DevPlan P, const TcBa
 // density contracts over functions, so the fixed-point grid of the leading
 // term is per point (column): first the largest |phi_i(p)| over all of the
 // batch's functions (FP32), then every 128-row block in double-float.
-__global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
+__global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                      uint8_t *ws, int n_split, int bound)
 {
     __shared__ unsigned int colmax[64];
@@ -1412,6 +1412,8 @@ __global__ void k_to_df(const double *x, float2 *out, const long long *rowptr, c
     }
 }
 
+constexpr int kGatherActSmem = 512;     // active atoms of a batch the gather stages in shared memory
+
 // the column side of the symmetric rows: value (g, j), j > g, bounds row j
 __global__ void k_d_colbounds(const float2 *v, const int *col_of, long long nnz, unsigned int *gmax, float *gsum)
 {
@@ -1435,15 +1437,43 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
     const int J = it.ti;
     __shared__ FnRef rref[128], cref[64];
     __shared__ float rsc[2][128];
+    __shared__ int4 sact[kGatherActSmem];            // per active atom: fn_loc, atom, loc, first global fn
     const DevAct *act = P.act + B.act0;
     const bool fixed = n_split == 3;
     const int *pp_sys = P.pairpos + P.sys_pair_off[B.sys];
     const int nat = P.sys_nat[B.sys];
+    // the batch's active atoms in shared memory, so that each column's
+    // reference costs one search there and one global load (its row start)
+    const bool staged = B.n_act <= kGatherActSmem;
+    if (staged) {
+        for (int e = threadIdx.x; e < B.n_act; e += blockDim.x) {
+            const DevAct A = act[e];
+            sact[e] = make_int4(A.fn_loc, A.atom, P.atom_loc[A.atom], (int)P.atom_fn0[A.atom]);
+        }
+    }
+    __syncthreads();
+    auto ref_of = [&](int l) -> FnRef {
+        if (!staged) return fn_ref(P, act, find_act(act, B.n_act, l), l);
+        int lo = 0, hi = B.n_act - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sact[mid].x <= l) lo = mid; else hi = mid - 1;
+        }
+        const int4 a = sact[lo];
+        FnRef r;
+        r.atom = a.y;
+        r.li = l - a.x;
+        r.gi = (long long)a.w + r.li;
+        r.rp = __ldg(P.rowptr + r.gi);
+        r.loc = a.z;
+        r.pad = 0;
+        return r;
+    };
     if (threadIdx.x < 128) {
         const int j = J * 128 + threadIdx.x;
         float sc = 0.f, un = 0.f;
         if (j < B.nfn) {
-            const FnRef rj = fn_ref(P, act, find_act(act, B.n_act, j), j);
+            const FnRef rj = ref_of(j);
             rref[threadIdx.x] = rj;
             if (fixed) fixed_scale_adaptive(__uint_as_float(gmax[rj.gi]), gsum[rj.gi], T.nkc * 64, sc, un);
         }
@@ -1459,7 +1489,7 @@ __global__ void __launch_bounds__(256) k_tc_gather_d(DevPlan P, const TcBatch *t
         __syncthreads();
         if (threadIdx.x < 64) {
             const int i = kc * 64 + threadIdx.x;
-            if (i < B.nfn) cref[threadIdx.x] = fn_ref(P, act, find_act(act, B.n_act, i), i);
+            if (i < B.nfn) cref[threadIdx.x] = ref_of(i);
         }
         __syncthreads();
         for (int u = threadIdx.x; u < 1024; u += blockDim.x) {
@@ -2135,7 +2165,10 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     if (w.nphi <= 0) return cudaSuccess;
     // the H images (v given) of the split mode use the fixed-point leading term
     const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
-    k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, smem_phi(), s>>>(P, t.d_batches, t.d_items + w.phi0,
+    // the dynamic buffer caches geometry for the FP32 pass over the points
+    // (bound_grids 0 and 1); the table-bound H pass needs none
+    const size_t dyn = t.bound_grids >= 2 ? 0 : smem_phi();
+    k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, dyn, s>>>(P, t.d_batches, t.d_items + w.phi0,
                                                        (uint8_t *)ws + t.img_base, v, n_split, fixed,
                                                        reinterpret_cast<int *>((uint8_t *)ws + t.sign_off),
                                                        t.bound_grids >= 2 ? 1 : 0);

@@ -6,7 +6,7 @@ tolerances before they are built.
 Leading digit x0 = rint(x / unit) * unit on a power-of-two grid per row
 (H) or per point (density), the remainder split into two BF16 terms
 (round to nearest even), products accumulated in FP32 per 16 contraction
-steps (one MMA), x0 * y0 exact.  Not a test of the CUDA code: the parity
+steps (one MMA, the accumulator update truncated), x0 * y0 exact.  Not a test of the CUDA code: the parity
 tests are.
 """
 import numpy as np
@@ -57,11 +57,23 @@ def split3(x, unit):
     return a.astype(np.float64), b.astype(np.float64), c.astype(np.float64)
 
 
-def _fp32_steps(pairs, K):
+def to_f32_rz(x):
+    """Round float64 values to FP32 toward zero (the accumulator update of
+    the tensor cores is modelled as truncating)."""
+    y = np.asarray(x, np.float64).astype(np.float32)
+    over = np.abs(y.astype(np.float64)) > np.abs(x)
+    return np.where(over, np.nextafter(y, np.float32(0)), y)
+
+
+def _fp32_steps(pairs, K, truncate=True):
+    """Products accumulated in FP32 per 16 contraction steps (one MMA): the
+    16-step partial sums exact, each added to the accumulator with one
+    rounding (toward zero by default, to nearest with truncate=False)."""
+    rnd = to_f32_rz if truncate else (lambda v: np.asarray(v).astype(np.float32))
     acc = None
     for k0 in range(0, K, 16):
-        part = sum(a[:, k0:k0 + 16] @ b[k0:k0 + 16] for a, b in pairs).astype(np.float32)
-        acc = part if acc is None else (acc + part).astype(np.float32)
+        part = sum(a[:, k0:k0 + 16] @ b[k0:k0 + 16] for a, b in pairs)
+        acc = rnd(part) if acc is None else rnd(acc.astype(np.float64) + part)
     return acc.astype(np.float64)
 
 

@@ -20,7 +20,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 TOL_FP64 = 1e-11
 TOL_SPLIT_H = 1e-7
 TOL_SPLIT_N = 1e-7
-TOL_BF16_H = 2e-2
+TOL_BF16_H = 2e-4        # plain BF16: twice the error measured on GB300 (9.8e-5 Ha)
 
 
 @pytest.fixture(scope="module")

@@ -7,7 +7,8 @@ are compared element by element on the stored pattern (H), point by point
 * FP64 path: 1e-11 relative to max|H| (rounding order only).
 * split BF16: max |dH_ij| <= 1e-7 Ha and density relative L2 <= 1e-7 (the
   accuracy targets the method sets for the split contractions).
-* plain BF16: max |dH_ij| <= 2e-2 Ha (reported, a sanity bound only).
+* plain BF16: max |dH_ij| <= 4e-3 Ha, twice the largest error measured on
+  these cases on GB300 (1.9e-3 Ha on water, 0.7-1.0e-3 on the others).
 """
 import numpy as np
 import pytest
@@ -21,7 +22,7 @@ pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-11
 TOL_SPLIT_H = 1e-7
 TOL_SPLIT_N = 1e-7
-TOL_BF16_H = 2e-2
+TOL_BF16_H = 4e-3        # plain BF16: twice the worst measured case (water, 1.9e-3 Ha)
 TOL_ADJ_DV = 1e-6        # split adjoint: max |d dv| / max |dv| (a random G: n_G changes sign)
 TOL_ADJ_DR = 1e-6        # split adjoint: max |d dR| / max |dR| (FP32 gradients)
 TOL_BF16_ADJ = 2e-2      # plain BF16 adjoint, both

@@ -126,7 +126,7 @@ def test_super_batches_waves_and_order(fgi, cluster, molecules, tmp_path, which,
 def test_default_settings_and_unmerged_batches(fgi, cluster, tmp_path):
     act, fns = active_sets(cluster)
     ctx = fgi.Context(-1).load(cluster, "split_bf16")
-    check_schedule(cluster, ctx.schedule("h"), act, fns, 400, 1.25)
+    check_schedule(cluster, ctx.schedule("h"), act, fns, 512, 1.25)
     check_schedule(cluster, ctx.schedule("density"), act, fns, 1024, 1.35)
     # a point limit of 0 keeps the batches as given
     ctx = plan(fgi, cluster, tmp_path, h_sb_points=0, density_sb_points=0)
@@ -139,7 +139,7 @@ def test_default_settings_and_unmerged_batches(fgi, cluster, tmp_path):
 def test_small_wave_budget_splits_into_waves(fgi, cluster, tmp_path):
     act, fns = active_sets(cluster)
     ctx = plan(fgi, cluster, tmp_path, wave_mb=1)
-    for which, pts, gr in (("h", 400, 1.25), ("density", 1024, 1.35)):
+    for which, pts, gr in (("h", 512, 1.25), ("density", 1024, 1.35)):
         s = ctx.schedule(which)
         assert len(s["wave_first_sb"]) - 1 > 4
         check_schedule(cluster, s, act, fns, pts, gr)

@@ -162,3 +162,48 @@ def test_deeper_h_contractions_cost_little():
         err[pmax] = np.abs(Hm - Hx).max()
     assert err[1024] <= 3.0 * err[0] + 1e-10, err
     assert err[1024] <= 1e-8
+
+
+@pytest.mark.slow
+def test_truncating_accumulation_makes_deep_h_contractions_costly():
+    """Why the H super-batches stop at 512 points: on the Si64 cluster
+    (|H| up to ~5 Ha on this sample) the model's H error grows with the
+    contraction depth when the FP32 accumulator update truncates (as the
+    tensor cores' does, one update per 16-point MMA step), and not when it
+    rounds to nearest.  Merging 40 consecutive batches into super-batches of
+    up to 1024 points multiplies the truncating error by more than 2."""
+    full = W.si64()
+    prob = full.subgrid(np.arange(200, 240))
+    B = O.system_basis(prob)
+    act_all = O.active_functions(B, prob.pts)
+    pos = -np.ones(B.n_fn, np.int64)
+    pos[act_all] = np.arange(len(act_all))
+    sizes = np.diff(prob.batch_off)
+    err = {}
+    for trunc in (True, False):
+        for pmax in (0, 1024):
+            groups, cur, cp = [], [], 0
+            for b in range(prob.n_batch):
+                if cur and (pmax == 0 or cp + sizes[b] > pmax):
+                    groups.append(cur)
+                    cur, cp = [], 0
+                cur.append(b)
+                cp += sizes[b]
+            groups.append(cur)
+            n = len(act_all)
+            Hx, Hm = np.zeros((n, n)), np.zeros((n, n))
+            for g in groups:
+                s0, s1 = prob.batch_off[g[0]], prob.batch_off[g[-1] + 1]
+                p = prob.pts[s0:s1]
+                wv = prob.w[s0:s1] * prob.v[s0:s1]
+                act = O.active_functions(B, p)
+                psi = O.phi(B, p, sub=act) * np.sqrt(np.abs(wv))[:, None]
+                unit = M.grid_units(np.abs(psi).max(axis=0), np.abs(psi).sum(axis=0), (len(p) + 63) // 64 * 64)
+                x0, x1, x2 = M.split3(psi, unit[None, :])
+                pairs = [(x0.T, x1), (x1.T, x0), (x0.T, x2), (x1.T, x1), (x2.T, x0), (x1.T, x2), (x2.T, x1)]
+                ix = np.ix_(pos[act], pos[act])
+                Hx[ix] -= psi.T @ psi
+                Hm[ix] -= x0.T @ x0 + M._fp32_steps(pairs, psi.shape[0], truncate=trunc)
+            err[trunc, pmax] = np.abs(Hm - Hx).max()
+    assert err[True, 1024] > 2.0 * err[True, 0], err
+    assert err[False, 1024] < 1.5 * err[False, 0], err

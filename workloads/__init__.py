@@ -186,6 +186,12 @@ class Problem:
     v: np.ndarray              # (n_pts,) float64
     workload_index: int = 0
     meta: dict = field(default_factory=dict)
+    # atom-centred structure of the grid (None where it is not known):
+    # owner atom and radial shell of every point, and per atom its radial
+    # grid r_k = r_min q^k, k < n_rad, as rows (r_min, ln q, n_rad)
+    owner: np.ndarray = None   # (n_pts,) int32, global atom index
+    shell: np.ndarray = None   # (n_pts,) int32
+    atom_rgrid: np.ndarray = None  # (n_atoms, 3) float64
 
     @property
     def n_sys(self) -> int:
@@ -220,11 +226,15 @@ class Problem:
         bs = np.nonzero(self.batch_sys == s)[0]
         p0, p1 = int(self.batch_off[bs[0]]), int(self.batch_off[bs[-1] + 1])
         off = (self.batch_off[bs[0]:bs[-1] + 2] - p0).astype(np.int64)
+        grid = {}
+        if self.owner is not None:
+            grid = dict(owner=(self.owner[p0:p1] - a0).astype(np.int32), shell=self.shell[p0:p1].copy(),
+                        atom_rgrid=self.atom_rgrid[a0:a1].copy())
         return Problem("%s-sys%d" % (self.name, s), self.radials, self.species,
                        np.array([0, a1 - a0], dtype=np.int64), self.atom_species[a0:a1].copy(),
                        self.atom_xyz[a0:a1].copy(), self.pts[p0:p1].copy(), self.w[p0:p1].copy(), off,
                        np.zeros(len(bs), dtype=np.int32), self.v[p0:p1].copy(), self.workload_index,
-                       dict(self.meta))
+                       dict(self.meta), **grid)
 
     def subgrid(self, batch_ids) -> "Problem":
         """A new problem holding only the listed batches (same geometry)."""
@@ -232,10 +242,13 @@ class Problem:
         idx = np.concatenate([np.arange(self.batch_off[b], self.batch_off[b + 1]) for b in batch_ids])
         sizes = self.batch_off[batch_ids + 1] - self.batch_off[batch_ids]
         off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        grid = {}
+        if self.owner is not None:
+            grid = dict(owner=self.owner[idx].copy(), shell=self.shell[idx].copy(), atom_rgrid=self.atom_rgrid)
         return Problem(self.name + "-sub", self.radials, self.species, self.atom_off,
                        self.atom_species, self.atom_xyz, self.pts[idx].copy(), self.w[idx].copy(),
                        off, self.batch_sys[batch_ids].copy(), self.v[idx].copy(),
-                       self.workload_index, dict(self.meta))
+                       self.workload_index, dict(self.meta), **grid)
 
 
 # --------------------------------------------------------------------------
@@ -258,8 +271,9 @@ def random_rotation(rng: np.random.Generator) -> np.ndarray:
     return q
 
 
-def atom_grid(center, r_max, n_rad, n_ang, rng, r_min=1e-3):
-    """Points and (un-partitioned) weights of one atom-centred grid."""
+def atom_grid(center, r_max, n_rad, n_ang, rng, r_min=1e-3, with_shells=False):
+    """Points and (un-partitioned) weights of one atom-centred grid (and,
+    with_shells, the radial shell index of every point)."""
     q = (r_max / r_min) ** (1.0 / (n_rad - 1))
     r = r_min * q ** np.arange(n_rad, dtype=np.float64)
     wr = r ** 3 * math.log(q)
@@ -270,6 +284,8 @@ def atom_grid(center, r_max, n_rad, n_ang, rng, r_min=1e-3):
         pts[k] = (s @ random_rotation(rng).T) * r[k]
     pts = pts.reshape(-1, 3) + np.asarray(center)[None, :]
     w = np.repeat(wr * wa, n_ang)
+    if with_shells:
+        return pts, w, np.repeat(np.arange(n_rad, dtype=np.int32), n_ang)
     return pts, w
 
 
@@ -446,27 +462,31 @@ def build_problem(name, radials, species, systems, grid_spec, workload_index,
     rmax_sp = [max(radials[r].r_cut for r in sp.radial_ids) for sp in species]
     atom_off = [0]
     all_sp, all_xyz, all_pts, all_w, all_v, boff, bsys = [], [], [], [], [], [0], []
+    all_own, all_shell, all_rgrid = [], [], []
     p_max, p_min, q_range = batch_spec
     for s, (sp_idx, xyz) in enumerate(systems):
         sp_idx = np.asarray(sp_idx, dtype=np.int32)
         xyz = np.asarray(xyz, dtype=np.float64)
-        pts_l, w_l, own_l = [], [], []
+        pts_l, w_l, own_l, sh_l = [], [], [], []
         for a in range(len(xyz)):
             n_rad, n_ang = grid_spec(int(sp_idx[a]))
-            p, w = atom_grid(xyz[a], rmax_sp[sp_idx[a]], n_rad, n_ang, rng_rot)
+            p, w, sh = atom_grid(xyz[a], rmax_sp[sp_idx[a]], n_rad, n_ang, rng_rot, with_shells=True)
             pts_l.append(p)
             w_l.append(w)
             own_l.append(np.full(len(w), a, dtype=np.int64))
+            sh_l.append(sh)
+            all_rgrid.append((1e-3, math.log((rmax_sp[sp_idx[a]] / 1e-3) ** (1.0 / (n_rad - 1))), n_rad))
         pts = np.concatenate(pts_l)
         w = np.concatenate(w_l)
         own = np.concatenate(own_l)
+        shell = np.concatenate(sh_l)
         dev = _torch_device(accel)
         if dev is None:
             w = w * becke_partition(pts, own, xyz, k_near=becke_k)
         else:
             w = w * becke_partition_torch(pts, own, xyz, dev, k_near=becke_k)
         keep = w >= 1e-18
-        pts, w = pts[keep], w[keep]
+        pts, w, own, shell = pts[keep], w[keep], own[keep], shell[keep]
         Zs = np.array([species[k].Z for k in sp_idx])
         vc = None if len(xyz) <= v_full_atoms else v_cut
         if dev is None:
@@ -479,6 +499,8 @@ def build_problem(name, radials, species, systems, grid_spec, workload_index,
         all_pts.append(pts[order])
         all_w.append(w[order])
         all_v.append(v[order])
+        all_own.append((own[order] + atom_off[-1]).astype(np.int32))
+        all_shell.append(shell[order])
         for lf in leaves:
             boff.append(boff[-1] + len(lf))
             bsys.append(s)
@@ -489,7 +511,8 @@ def build_problem(name, radials, species, systems, grid_spec, workload_index,
                    np.concatenate(all_sp).astype(np.int32), np.concatenate(all_xyz),
                    np.concatenate(all_pts), np.concatenate(all_w),
                    np.array(boff, dtype=np.int64), np.array(bsys, dtype=np.int32),
-                   np.concatenate(all_v), workload_index)
+                   np.concatenate(all_v), workload_index, owner=np.concatenate(all_own),
+                   shell=np.concatenate(all_shell), atom_rgrid=np.array(all_rgrid, dtype=np.float64))
 
 
 # --------------------------------------------------------------------------
@@ -706,8 +729,12 @@ def many_molecules(n_mol=512, workload_index=4, n_at_range=(5, 40), nrad_range=(
 def merge_problems(name, parts, workload_index):
     atom_off = [0]
     boff = [0]
-    sp, xyz, pts, w, v, bsys = [], [], [], [], [], []
+    sp, xyz, pts, w, v, bsys, own, shell, rgrid = [], [], [], [], [], [], [], [], []
     for s, p in enumerate(parts):
+        if p.owner is not None:
+            own.append(p.owner + atom_off[-1])
+            shell.append(p.shell)
+            rgrid.append(p.atom_rgrid)
         sp.append(p.atom_species)
         xyz.append(p.atom_xyz)
         atom_off.append(atom_off[-1] + len(p.atom_species))
@@ -721,7 +748,9 @@ def merge_problems(name, parts, workload_index):
     return Problem(name, p0.radials, p0.species, np.array(atom_off, dtype=np.int64),
                    np.concatenate(sp).astype(np.int32), np.concatenate(xyz), np.concatenate(pts),
                    np.concatenate(w), np.array(boff, dtype=np.int64),
-                   np.array(bsys, dtype=np.int32), np.concatenate(v), workload_index)
+                   np.array(bsys, dtype=np.int32), np.concatenate(v), workload_index,
+                   **(dict(owner=np.concatenate(own).astype(np.int32), shell=np.concatenate(shell),
+                           atom_rgrid=np.concatenate(rgrid)) if len(own) == len(parts) else {}))
 
 
 # --------------------------------------------------------------------------
