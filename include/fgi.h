@@ -254,6 +254,45 @@ int fgi_density(fgi_ctx *ctx, const double *d_dev, double *n_dev, double *traces
 int fgi_adjoint(fgi_ctx *ctx, const double *g_dev, const double *v_dev, double *dv_dev,
                 double *dR_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* The grid's atom-centred structure, for fgi_hartree: owner[n_pts] (host,
+   int32) the atom whose grid each point came from (global atom index, in the
+   point's own system; -1 for a point of no atom grid), shell[n_pts] its
+   radial shell on that grid, and per atom (host, n_atoms entries) the radial
+   grid r_k = r_min[a] exp(k ln_q[a]), k = 0 .. n_rad[a]-1 (n_rad >= 4).  The point weights
+   given to fgi_set_grid are then read as (partition weight) x r_k^3 ln q x
+   (angular weight).  Call after fgi_set_grid; fgi_set_systems or
+   fgi_set_grid discard it.  Copies the tables to the device (a setup call:
+   it allocates).  FGI_ERR_ARG for an owner outside the point's system or a
+   shell beyond its grid. */
+int fgi_set_atom_grids(fgi_ctx *ctx, const int32_t *owner, const int32_t *shell, const double *r_min,
+                       const double *ln_q, const int32_t *n_rad);
+
+/* Bytes of device scratch fgi_hartree needs (any l_max). */
+int fgi_hartree_workspace_size(fgi_ctx *ctx, size_t *bytes);
+
+/* The step upstream of the integration: the Hartree potential of the density
+   on the grid, vh_dev[p] = int n(r') / |r_p - r'| dr' (Hartree, Bohr), by the
+   multipole method of Becke & Dickson (J. Chem. Phys. 89, 2993 (1988)) and
+   Delley (J. Chem. Phys. 92, 508 (1990)) -- the electrostatic potential that
+   the paper's Fig. 4 caption lists as not yet accelerated on GPUs:
+     1. rho_a,lm(r_k) = sum over the points of atom a's shell k of
+        w_p / (r_k^3 ln q) n_p Y_lm (the partitioned angular quadrature);
+     2. per (a, l, m) the radial Poisson equation,
+        V(r) = 4 pi/(2l+1) [r^-(l+1) int_0^r rho r'^(l+2) dr' + r^l int_r^inf rho r'^(1-l) dr'],
+        the partial integrals in ln r interval by interval by the integral
+        of the cubic through the four nearest shells (plus rho(r_0)
+        r_0^(l+3)/(l+3) inside the first shell);
+     3. vh(r) = sum over the atoms of the point's system and l <= l_max of
+        V_a,lm(|r - R_a|) Y_lm, with V between shells by 4-point Lagrange
+        interpolation in the fractional shell index, 4 pi/(2l+1) Q_lm /
+        d^(l+1) beyond the last shell, V(r_0) (d/r_0)^l inside the first.
+   n_dev, vh_dev: device [n_pts] FP64 in the caller's point order;
+   0 <= l_max <= 6 (FGI_ERR_UNSUPPORTED otherwise).  FP64 throughout; the
+   evaluation visits every (point, atom) pair of a system.  Needs a plan and
+   fgi_set_atom_grids. */
+int fgi_hartree(fgi_ctx *ctx, const double *n_dev, double *vh_dev, int l_max, void *ws, size_t ws_bytes,
+                void *stream);
+
 /* out_dev[s] = sum_ij A_ij B_ij over system s's full symmetric matrices
    stored as upper triangles a_dev, b_dev (device [nnz] FP64): tr(DS) with
    A = D, B = S, or the band energy with B = H.  FP64. */

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfgi.so")
-SOURCES = ["fgi_host.cpp", "fgi_f64.cu", "fgi_tc.cu", "fgi_noalloc.cu"]
+SOURCES = ["fgi_host.cpp", "fgi_f64.cu", "fgi_tc.cu", "fgi_noalloc.cu", "fgi_hartree.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,31 @@
+// The Hartree potential from the density on the grid (multipole method):
+// device tables and launcher.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fgi_internal.h"
+
+namespace fgi {
+
+// the grid's atom-centred structure on the device
+struct HartreeDev {
+    const int *owner = nullptr;          // [n_pts] owner atom (global index, -1: none)
+    const int *shell = nullptr;          // [n_pts] radial shell on the owner's grid
+    const long long *rad_off = nullptr;  // [n_atoms + 1] first shell of each atom in the shell tables
+    const double2 *rgrid = nullptr;      // [n_atoms] (r_min, ln q): r_k = r_min exp(k ln q)
+    const int *nrad = nullptr;           // [n_atoms] shells per atom
+    const long long *sys_atom0 = nullptr;  // [n_sys + 1] first atom of each system
+    int n_atoms = 0;
+    long long n_shells = 0;
+};
+
+// scratch of one call: multipoles and potentials on the shells, exterior moments
+size_t hartree_ws_bytes(const HartreeDev &H);
+
+// v_H at every point of the grid from n (both device, caller's point order)
+cudaError_t launch_hartree(const DevPlan &P, const HartreeDev &H, int n_batch, long long n_pts, int l_max,
+                           const double *n, double *vh, double *ws, cudaStream_t s);
+
+}  // namespace fgi

@@ -14,6 +14,8 @@
 #include <vector>
 
 #include "fgi_bounds.h"
+#include "fgi_hartree.h"
+#include "fgi_ylm.cuh"
 #include "fgi_internal.h"
 #include "fgi_tc.h"
 #include "../../include/fgi.h"
@@ -140,6 +142,12 @@ struct fgi_ctx {
     TcPlan tc;                                // tensor-core plan of the H integration (the batches as given)
     TcPlan tcd;                               // tensor-core plan of the density (super-batches)
     TcPlan tca;                               // the density's super-batches with room for E (the adjoint)
+    // atom-centred structure of the grid (the Hartree potential)
+    bool have_atom_grids = false;
+    std::vector<int> hg_owner, hg_shell, hg_nrad;
+    std::vector<double> hg_rmin, hg_lnq;
+    char *d_hartree = nullptr;
+    HartreeDev hd{};
     // per-kernel CUDA-event profile
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -181,6 +189,14 @@ struct DeviceGuard {
         if (e_ != cudaSuccess)                                                              \
             return set_err(c, FGI_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));       \
     } while (0)
+
+void free_atom_grids(fgi_ctx *c)
+{
+    if (c->d_hartree) cudaFree(c->d_hartree);
+    c->d_hartree = nullptr;
+    c->hd = HartreeDev{};
+    c->have_atom_grids = false;
+}
 
 void free_device(fgi_ctx *c)
 {
@@ -949,6 +965,7 @@ int fgi_destroy(fgi_ctx *c)
     if (c->device >= 0) {
         DeviceGuard g(c->device);
         free_device(c);
+        free_atom_grids(c);
         for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     }
     delete c;
@@ -1018,6 +1035,10 @@ int fgi_set_systems(fgi_ctx *c, int n_sys, const int64_t *atom_off, const int *s
     c->atom_xyz.assign(xyz, xyz + 3 * na);
     c->have_systems = true;
     invalidate(c);
+    if (c->have_atom_grids) {
+        DeviceGuard g(c->device >= 0 ? c->device : 0);
+        free_atom_grids(c);
+    }
     return FGI_OK;
 }
 
@@ -1052,6 +1073,10 @@ int fgi_set_grid(fgi_ctx *c, int64_t n_pts, const double *xyz, const double *w, 
     c->batch_sys.assign(batch_sys, batch_sys + n_batch);
     c->have_grid = true;
     invalidate(c);
+    if (c->have_atom_grids) {
+        DeviceGuard g(c->device >= 0 ? c->device : 0);
+        free_atom_grids(c);
+    }
     return FGI_OK;
 }
 
@@ -1313,6 +1338,101 @@ int fgi_adjoint(fgi_ctx *c, const double *gv, const double *v, double *dv, doubl
         CUDA_TRY(c, launch_adjoint_grad(P, w.b0, w.nb, e_ws, v, dR, s));
     }
     CUDA_TRY(c, launch_scale_by_weight(P, c->n_pts, dv, s));
+    return FGI_OK;
+}
+
+int fgi_set_atom_grids(fgi_ctx *c, const int32_t *owner, const int32_t *shell, const double *r_min,
+                       const double *ln_q, const int32_t *n_rad)
+{
+    if (!c) return FGI_ERR_ARG;
+    if (!c->have_systems || !c->have_grid) return set_err(c, FGI_ERR_STATE, "set systems and grid first");
+    const int n_at = (int)c->atom_species.size();
+    if ((c->n_pts > 0 && (!owner || !shell)) || (n_at > 0 && (!r_min || !ln_q || !n_rad)))
+        return set_err(c, FGI_ERR_ARG, "atom grids: NULL argument");
+    for (int a = 0; a < n_at; a++)
+        if (!(r_min[a] > 0.0) || !(ln_q[a] > 0.0) || !std::isfinite(r_min[a]) || !std::isfinite(ln_q[a]) || n_rad[a] < 4)
+            return set_err(c, FGI_ERR_ARG, "atom grids: atom %d needs r_min > 0, ln q > 0, n_rad >= 4", a);
+    // every point's owner lies in the point's own system, its shell on the owner's grid
+    std::vector<int> pt_sys((size_t)c->n_pts);
+    for (size_t b = 0; b + 1 < c->batch_off.size(); b++)
+        for (int64_t p = c->batch_off[b]; p < c->batch_off[b + 1]; p++) pt_sys[(size_t)p] = c->batch_sys[b];
+    for (int64_t p = 0; p < c->n_pts; p++) {
+        const int a = owner[p];
+        if (a == -1) continue;
+        if (a < 0 || a >= n_at || shell[p] < 0 || shell[p] >= n_rad[a])
+            return set_err(c, FGI_ERR_ARG, "atom grids: point %lld has owner %d, shell %d", (long long)p, a,
+                           (int)shell[p]);
+        if (a < c->atom_off[pt_sys[(size_t)p]] || a >= c->atom_off[pt_sys[(size_t)p] + 1])
+            return set_err(c, FGI_ERR_ARG, "atom grids: point %lld belongs to another system than its owner",
+                           (long long)p);
+    }
+    if (c->device >= 0) {
+        DeviceGuard g(c->device);
+        free_atom_grids(c);
+    }
+    c->hg_owner.assign(owner, owner + c->n_pts);
+    c->hg_shell.assign(shell, shell + c->n_pts);
+    c->hg_rmin.assign(r_min, r_min + n_at);
+    c->hg_lnq.assign(ln_q, ln_q + n_at);
+    c->hg_nrad.assign(n_rad, n_rad + n_at);
+    std::vector<long long> rad_off(n_at + 1, 0);
+    for (int a = 0; a < n_at; a++) rad_off[a + 1] = rad_off[a] + n_rad[a];
+    std::vector<double2> rgrid(n_at);
+    for (int a = 0; a < n_at; a++) rgrid[a] = make_double2(r_min[a], ln_q[a]);
+    std::vector<long long> sys_atom0(c->atom_off.begin(), c->atom_off.end());
+    c->hd.n_atoms = n_at;
+    c->hd.n_shells = rad_off[n_at];
+    if (c->device >= 0) {
+        DeviceGuard g(c->device);
+        const size_t s_own = align_up(4 * (size_t)c->n_pts + 4, 256), s_off = align_up(8 * (size_t)(n_at + 1), 256),
+                     s_rg = align_up(16 * (size_t)n_at + 16, 256), s_nr = align_up(4 * (size_t)n_at + 4, 256),
+                     s_sys = align_up(8 * sys_atom0.size(), 256);
+        const size_t tot = 2 * s_own + s_off + s_rg + s_nr + s_sys;
+        CUDA_TRY(c, cudaMalloc((void **)&c->d_hartree, tot));
+        char *b = c->d_hartree;
+        CUDA_TRY(c, cudaMemcpy(b, owner, 4 * (size_t)c->n_pts, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + s_own, shell, 4 * (size_t)c->n_pts, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own, rad_off.data(), 8 * rad_off.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off, rgrid.data(), 16 * (size_t)n_at, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off + s_rg, n_rad, 4 * (size_t)n_at, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off + s_rg + s_nr, sys_atom0.data(), 8 * sys_atom0.size(),
+                               cudaMemcpyHostToDevice));
+        c->hd.owner = (const int *)b;
+        c->hd.shell = (const int *)(b + s_own);
+        c->hd.rad_off = (const long long *)(b + 2 * s_own);
+        c->hd.rgrid = (const double2 *)(b + 2 * s_own + s_off);
+        c->hd.nrad = (const int *)(b + 2 * s_own + s_off + s_rg);
+        c->hd.sys_atom0 = (const long long *)(b + 2 * s_own + s_off + s_rg + s_nr);
+    }
+    c->have_atom_grids = true;
+    return FGI_OK;
+}
+
+int fgi_hartree_workspace_size(fgi_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return FGI_ERR_ARG;
+    if (!c->have_atom_grids) return set_err(c, FGI_ERR_STATE, "call fgi_set_atom_grids first");
+    *bytes = hartree_ws_bytes(c->hd);
+    return FGI_OK;
+}
+
+int fgi_hartree(fgi_ctx *c, const double *n, double *vh, int l_max, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc = check_compute(c);
+    if (rc) return rc;
+    if (!c->have_atom_grids) return set_err(c, FGI_ERR_STATE, "call fgi_set_atom_grids first");
+    if (!n || !vh) return set_err(c, FGI_ERR_ARG, "n or vh is NULL");
+    if (l_max < 0 || l_max > kHartreeLmax)
+        return set_err(c, FGI_ERR_UNSUPPORTED, "l_max = %d; 0 <= l_max <= %d supported", l_max, kHartreeLmax);
+    if (!ws || ((uintptr_t)ws & 255)) return set_err(c, FGI_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+    if (ws_bytes < hartree_ws_bytes(c->hd))
+        return set_err(c, FGI_ERR_WORKSPACE, "workspace of %zu bytes, need %zu", ws_bytes, hartree_ws_bytes(c->hd));
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevPlan P = c->dp;
+    P.batches = c->d_batches_f64;
+    ProfScope ps(c, s, 4, 0.0, 8.0 * (double)c->n_pts, 3);
+    CUDA_TRY(c, launch_hartree(P, c->hd, (int)c->batch_sys.size(), c->n_pts, l_max, n, vh, (double *)ws, s));
     return FGI_OK;
 }
 

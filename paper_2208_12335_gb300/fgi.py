@@ -71,6 +71,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgi_get_batch_work": ([P, I64, P, P], I),
         "fgi_selftest_wait_timeout": ([P, P], I),
         "fgi_get_schedule": ([P, I, C.POINTER(I64), C.POINTER(I64), P, P, P, P, P], I),
+        "fgi_set_atom_grids": ([P, P, P, P, P, P], I),
+        "fgi_hartree_workspace_size": ([P, C.POINTER(C.c_size_t)], I),
+        "fgi_hartree": ([P, P, P, I, P, C.c_size_t, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +196,45 @@ class Context:
                                            _ptr(batch_off), _ptr(batch_sys)))
         self._n_batch = len(batch_off) - 1
 
+    def set_atom_grids(self, owner, shell, atom_rgrid):
+        """The grid's atom-centred structure for the Hartree potential: owner
+        atom and radial shell of every point, and per atom rows (r_min, ln q,
+        n_rad) of its radial grid r_k = r_min exp(k ln q)."""
+        owner = _np(owner, np.int32)
+        shell = _np(shell, np.int32)
+        rg = np.asarray(atom_rgrid, dtype=np.float64).reshape(-1, 3)
+        r_min = np.ascontiguousarray(rg[:, 0])
+        ln_q = np.ascontiguousarray(rg[:, 1])
+        n_rad = np.ascontiguousarray(rg[:, 2].astype(np.int32))
+        self._check(self._lib.fgi_set_atom_grids(self._h, _ptr(owner), _ptr(shell), _ptr(r_min), _ptr(ln_q),
+                                                 _ptr(n_rad)))
+        self._hws = None
+
+    def hartree_workspace_size(self) -> int:
+        out = C.c_size_t()
+        self._check(self._lib.fgi_hartree_workspace_size(self._h, C.byref(out)))
+        return out.value
+
+    def hartree(self, n, l_max=4, vh=None, ws=None, stream=None):
+        """The Hartree potential of the density n on the grid (device FP64
+        [n_pts] in, a new or given [n_pts] tensor out), multipoles up to l_max."""
+        if getattr(self, "_pending_grids", None) is not None:
+            self.set_atom_grids(*self._pending_grids)
+            self._pending_grids = None
+        n_pts = self.sizes()[2]
+        _dev_f64(n, n_pts, "n")
+        if vh is None:
+            vh = torch.empty(n_pts, dtype=torch.float64, device=n.device)
+        _dev_f64(vh, n_pts, "vh")
+        if ws is None:
+            if getattr(self, "_hws", None) is None:
+                self._hws = torch.empty(max(256, self.hartree_workspace_size()), dtype=torch.uint8,
+                                        device=n.device)
+            ws = self._hws
+        self._check(self._lib.fgi_hartree(self._h, _ptr(n), _ptr(vh), int(l_max), _ptr(ws), ws.numel(),
+                                          _stream(stream)))
+        return vh
+
     def plan(self, precision="fp64", tune_path=None):
         """Build the plan (active functions, pattern, tile lists, device copies)
         for precision 'fp64', 'split_bf16' or 'bf16'; tune_path: optional
@@ -213,6 +255,10 @@ class Context:
             self.add_species(sp.Z, [rid[k] for k in sp.radial_ids])
         self.set_systems(problem.atom_off, problem.atom_species, problem.atom_xyz)
         self.set_grid(problem.pts, problem.w, problem.batch_off, problem.batch_sys)
+        # the grid's atom-centred structure goes to the library at the first
+        # Hartree call (the integration does not need it)
+        self._pending_grids = ((problem.owner, problem.shell, problem.atom_rgrid)
+                               if getattr(problem, "owner", None) is not None else None)
         self.plan(precision, tune_path)
         return self
 

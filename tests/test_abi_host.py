@@ -309,3 +309,38 @@ def test_autograd_forward_refuses_a_moved_geometry(fgi, water):
     # argument check wants a device tensor
     with pytest.raises(TypeError, match="CUDA"):
         fgi.integrate(ctx, v, torch.from_numpy(water.atom_xyz.copy()))
+
+
+def test_atom_grid_structure_is_checked(fgi, water):
+    """fgi_set_atom_grids: every point's owner must be an atom of its own
+    system and its shell on that atom's radial grid; the Hartree call needs
+    a device (a host-only context reports FGI_ERR_STATE)."""
+    ctx = fgi.Context(-1).load(water, "fp64")
+    ctx.set_atom_grids(water.owner, water.shell, water.atom_rgrid)
+    assert ctx.hartree_workspace_size() >= 8 * water.atom_rgrid[:, 2].sum()
+    bad = water.shell.copy()
+    bad[3] = int(water.atom_rgrid[water.owner[3], 2])          # one past the owner's last shell
+    with pytest.raises(fgi.FGIError) as e:
+        ctx.set_atom_grids(water.owner, bad, water.atom_rgrid)
+    assert e.value.code == -1
+    own = water.owner.copy()
+    own[0] = 7                                                 # no such atom
+    with pytest.raises(fgi.FGIError):
+        ctx.set_atom_grids(own, water.shell, water.atom_rgrid)
+    rg = water.atom_rgrid.copy()
+    rg[1, 1] = -0.1                                            # ln q must be positive
+    with pytest.raises(fgi.FGIError):
+        ctx.set_atom_grids(water.owner, water.shell, rg)
+    lib = fgi.lib()
+    assert lib.fgi_hartree(ctx._h, None, None, 4, None, 0, None) == -2
+
+
+def test_atom_grid_owner_must_share_the_point_system(fgi):
+    prob = W.many_molecules(n_mol=2, n_at_range=(3, 3), nrad_range=(8, 8), nang_choices=(14,))
+    ctx = fgi.Context(-1).load(prob, "fp64")
+    ctx.set_atom_grids(prob.owner, prob.shell, prob.atom_rgrid)
+    own = prob.owner.copy()
+    p = int(prob.system_points(1)[0])
+    own[p] = 0                                                 # an atom of system 0
+    with pytest.raises(fgi.FGIError):
+        ctx.set_atom_grids(own, prob.shell, prob.atom_rgrid)
