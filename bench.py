@@ -334,6 +334,8 @@ def main():
                          "captured graph against a per-molecule FP64 loop); 0: skip")
     ap.add_argument("--adjoint-steps", type=int, default=2,
                     help="also time the adjoint (dL/dv, dL/dR) on the same plan (0: skip)")
+    ap.add_argument("--hartree-steps", type=int, default=2,
+                    help="also time the Hartree potential of the step's density (0: skip)")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-batches", type=int, default=12)
@@ -551,6 +553,32 @@ def main():
                "unit": UNIT, "path": args.precision, "steps": args.adjoint_steps,
                "what": "dL/dv and dL/dR of L = sum_k g_k h_k, seeded random g on the H pattern"}
 
+    # the step upstream: the Hartree potential of the step's density on the
+    # same grid (multipole method, l_max 4; FP64 l = 0, FP32 l >= 1 terms)
+    hart = None
+    if args.hartree_steps > 0 and getattr(prob, "owner", None) is not None:
+        step()
+        ctx.sync()
+        n_cur = n.clone()
+        vh = ctx.hartree(n_cur, l_max=4)
+        ctx.sync()
+        th = timed(args.hartree_steps, lambda: ctx.hartree(n_cur, l_max=4, vh=vh))
+        hms = statistics.mean(th)
+        pairs = sum(int(np.sum(np.diff(prob.batch_off)[prob.batch_sys == s_])) *
+                    int(prob.atom_off[s_ + 1] - prob.atom_off[s_]) for s_ in range(prob.n_sys))
+        hart = {"ms_per_call": hms, "value": n_pts / (hms * 1e-3), "unit": UNIT, "l_max": 4,
+                "point_atom_pairs_per_s": pairs / (hms * 1e-3), "steps": args.hartree_steps,
+                "what": "v_H of the step's density n on the grid (multipoles on each atom's shells, "
+                        "radial Poisson equation, evaluation at every point over every atom)"}
+        if not args.no_check and n_pts <= 2_000_000 and rank == 0:
+            import oracle.hartree as OH
+            idx = np.sort(np.random.default_rng(11).choice(n_pts, min(n_pts, 400), replace=False))
+            ref, bound = OH.hartree(prob, n_cur.cpu().numpy(), l_max=4, pts_idx=idx, l1_bound=True)
+            err = np.abs(vh.cpu().numpy()[idx] - ref)
+            hart["vs_oracle_sample"] = {"points": len(idx), "max_abs": float(err.max()),
+                                        "max_rel_to_max_v": float(err.max() / np.abs(ref).max()),
+                                        "max_err_over_l1_scale": float(np.max(err / np.maximum(bound, 1e-300)))}
+
     def many_leg(n_mol):
         """The many-instance workload: n_mol independent molecules in one plan,
         the split-BF16 step (H + density of every molecule) replayed as one
@@ -766,6 +794,7 @@ def main():
                "bf16_path": variants.get("bf16"),
                "many_instance": many,
                "adjoint": adj,
+               "hartree": hart,
                "fp64_per_molecule_loop": fp64_loop,
                "errors_vs_oracle": errors,
                "clocks": clk.summary(),

@@ -119,8 +119,11 @@ class HartreeTables:
             self.lnq.append(ln_q)
         self.ls = ls
 
-    def radial(self, a: int, d: np.ndarray) -> np.ndarray:
-        """V_a,lm at distances d [n]: (n, L)."""
+    def radial(self, a: int, d: np.ndarray, magnitude: bool = False) -> np.ndarray:
+        """V_a,lm at distances d [n]: (n, L).  magnitude: instead the size of
+        what is summed for each entry (|V| beyond and inside the grid, the sum
+        of |weight x V| over the four interpolation nodes between shells), the
+        scale of the rounding error of any evaluation of it."""
         V, r_k, ln_q = self.V[a], self.r[a], self.lnq[a]
         n_rad = len(r_k)
         out = np.empty((len(d), V.shape[1]))
@@ -132,6 +135,8 @@ class HartreeTables:
             out[far] = pref[None, :] * self.Q[a][None, :] / d[far][:, None] ** (self.ls[None, :] + 1.0)
         if near.any():
             out[near] = V[0][None, :] * (d[near][:, None] / r_k[0]) ** self.ls[None, :]
+        if magnitude:
+            out[far | near] = np.abs(out[far | near])
         if mid.any():
             x = np.log(d[mid] / r_k[0]) / ln_q
             i0 = np.clip(np.floor(x).astype(np.int64) - 1, 0, n_rad - 4)
@@ -142,18 +147,24 @@ class HartreeTables:
                 for m in range(4):
                     if m != j:
                         lj *= (t - m) / (j - m)
-                acc += lj[:, None] * V[i0 + j]
+                term = lj[:, None] * V[i0 + j]
+                acc += np.abs(term) if magnitude else term
             out[mid] = acc
         return out
 
-    def potential(self, pts: np.ndarray, sys_of_pts=None) -> np.ndarray:
+    def potential(self, pts: np.ndarray, sys_of_pts=None, l1_bound: bool = False):
         """v_H at arbitrary points (all of one system: sys_of_pts None means
-        system 0's atoms, else an int system index)."""
+        system 0's atoms, else an int system index).  l1_bound: also return,
+        per point, sum over atoms and l >= 1 of the magnitudes of the radial
+        terms (radial(magnitude=True)) times max |Y_lm| = sqrt((2l+1)/(4 pi))
+        (Unsold), the scale of a rounding error confined to the l >= 1 part."""
         prob = self.problem
         s = 0 if sys_of_pts is None else int(sys_of_pts)
         a0, a1 = int(prob.atom_off[s]), int(prob.atom_off[s + 1])
         pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
         v = np.zeros(len(pts))
+        bound = np.zeros(len(pts))
+        ymax = np.sqrt((2.0 * self.ls + 1.0) / (4.0 * math.pi)) * (self.ls >= 1)
         for a in range(a0, a1):
             dvec = pts - prob.atom_xyz[a][None, :]
             d = np.linalg.norm(dvec, axis=1)
@@ -162,21 +173,28 @@ class HartreeTables:
             Y[ok] = real_ylm(self.l_max, dvec[ok] / d[ok][:, None])
             Y[~ok, 0] = 1.0 / math.sqrt(4.0 * math.pi)
             v += np.sum(self.radial(a, d) * Y, axis=1)
-        return v
+            if l1_bound:
+                bound += np.sum(self.radial(a, d, magnitude=True) * ymax[None, :], axis=1)
+        return (v, bound) if l1_bound else v
 
 
-def hartree(problem, n: np.ndarray, l_max: int = 4, pts_idx=None) -> np.ndarray:
+def hartree(problem, n: np.ndarray, l_max: int = 4, pts_idx=None, l1_bound: bool = False):
     """v_H at the grid points (all, or the listed indices) of a problem whose
-    grid carries its atom-centred structure (owner, shell, atom_rgrid)."""
+    grid carries its atom-centred structure (owner, shell, atom_rgrid);
+    l1_bound: also the per-point scale of the l >= 1 terms
+    (HartreeTables.potential)."""
     if problem.owner is None:
         raise ValueError("the problem's grid carries no atom-centred structure")
     T = HartreeTables(problem, np.asarray(n, dtype=np.float64), l_max)
     idx = np.arange(problem.n_pts) if pts_idx is None else np.asarray(pts_idx)
     out = np.empty(len(idx))
+    bound = np.empty(len(idx))
     # points of each system see only that system's atoms
     bsys = np.repeat(problem.batch_sys, np.diff(problem.batch_off))
     for s in range(problem.n_sys):
         sel = np.nonzero(bsys[idx] == s)[0]
-        if len(sel):
+        if len(sel) and l1_bound:
+            out[sel], bound[sel] = T.potential(problem.pts[idx[sel]], s, l1_bound=True)
+        elif len(sel):
             out[sel] = T.potential(problem.pts[idx[sel]], s)
-    return out
+    return (out, bound) if l1_bound else out

@@ -2,21 +2,32 @@
 // density on the grid, v_H(r) = int n(r') / |r - r'| dr', by the multipole
 // method of Becke & Dickson (1988) and Delley (1990), which the NAO method
 // uses for the electrostatic potential (the paper's Fig. 4 caption notes that
-// this potential was not yet accelerated on GPUs).  FP64 throughout.
+// this potential was not yet accelerated on GPUs).
 //
-//  1. k_hartree_moments: per point p on atom a's radial shell k,
-//       rho_a,lm(r_k) += (w_p / (r_k^3 ln q)) n_p Y_lm(rhat_p)
-//     (w_p / (r_k^3 ln q) is the partitioned angular weight), FP64 atomics.
-//  2. k_hartree_radial: per (atom, l, m) the radial Poisson equation
+//  1. k_hartree_moments (FP64): per point p on atom a's radial shell k,
+//       rho~_a,lm(r_k) += (w_p / (r_k^3 ln q)) n_p A_lm(rhat_p)
+//     (w_p / (r_k^3 ln q) is the partitioned angular weight; A_lm = Y_lm / K_lm
+//     the unnormalised harmonics), FP64 atomics.
+//  2. k_hartree_radial (FP64): per (atom, l, m) the radial Poisson equation
 //       V(r) = 4 pi/(2l+1) [r^-(l+1) int_0^r rho r'^(l+2) dr' + r^l int_r^inf rho r'^(1-l) dr']
 //     with the partial integrals in x = ln r interval by interval, each by the
 //     integral of the cubic through its four nearest shells, plus
 //     rho(r_0) r_0^(l+3)/(l+3) inside the first shell; Q_lm = the whole inner
-//     integral (the exterior multipole moments).
+//     integral (the exterior multipole moments).  Stored with K_lm^2 folded in
+//     (Y_lm Y_lm-weighted sums become A_lm sums): l = 0 in FP64 (V) and as a
+//     double-float (Q, in a packed per-atom record with the atom's position),
+//     l >= 1 in FP32.
 //  3. k_hartree_eval: per point, over the atoms of its system, V_a,lm at the
-//     distance (4-point Lagrange interpolation in the fractional shell index
-//     inside the grid, 4 pi/(2l+1) Q_lm / d^(l+1) beyond the last shell,
-//     V(r_0) (d/r_0)^l inside the first) times Y_lm of the direction.
+//     distance times Y_lm of the direction: 4-point Lagrange interpolation in
+//     the fractional shell index inside the grid (l = 0 in FP64),
+//     4 pi/(2l+1) Q_lm / d^(l+1) beyond the last shell (l = 0 as a
+//     double-float: offset, distance and 1/d from the double-float point and
+//     atom positions), V(r_0) (d/r_0)^l inside the first shell.  The l >= 1
+//     terms (angular functions, their coefficients and sums) are FP32: each
+//     carries a relative error of a few FP32 roundings of the l >= 1 part,
+//     against the FP64 pipe's 1/64 rate on GB300.  The sum over atoms is a
+//     double-float.
+#include "fgi_dd.cuh"
 #include "fgi_hartree.h"
 #include "fgi_ylm.cuh"
 
@@ -24,7 +35,69 @@ namespace fgi {
 
 namespace {
 
-constexpr int kL = (kHartreeLmax + 1) * (kHartreeLmax + 1);
+constexpr int kL = (kHartreeLmax + 1) * (kHartreeLmax + 1);  // stride of the FP64 moment rows
+constexpr int kLf = kL - 1;                                     // stride of the FP32 l >= 1 rows
+
+struct HartreeTabs {
+    double *rho;      // [n_shells][kL]    unnormalised moments
+    double *Vd;       // [n_shells][kL]    scratch: inner part of V
+    double *F;        // [n_shells][kL]    scratch: inner integrand
+    float4 *rec;      // [n_atoms][3]      position (double-float), (last radius)^2, 4 pi K_00^2 Q_00
+    double *V0;       // [n_shells]        K_00^2 V_00
+    float *Vf;        // [n_shells][kLf]   K_lm^2 V_lm, l >= 1
+    float *Qf;        // [n_atoms][kLf]    4 pi/(2l+1) K_lm^2 Q_lm, l >= 1
+};
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+HartreeTabs carve(const HartreeDev &H, void *ws)
+{
+    char *b = (char *)ws;
+    HartreeTabs T;
+    T.rho = (double *)b;
+    b += al256(sizeof(double) * kL * (size_t)H.n_shells);
+    T.Vd = (double *)b;
+    b += al256(sizeof(double) * kL * (size_t)H.n_shells);
+    T.F = (double *)b;
+    b += al256(sizeof(double) * kL * (size_t)H.n_shells);
+    T.rec = (float4 *)b;
+    b += al256(sizeof(float4) * 3 * (size_t)H.n_atoms);
+    T.V0 = (double *)b;
+    b += al256(sizeof(double) * (size_t)H.n_shells);
+    T.Vf = (float *)b;
+    b += al256(sizeof(float) * kLf * (size_t)H.n_shells);
+    T.Qf = (float *)b;
+    return T;
+}
+
+__device__ __forceinline__ df dfa(df a, df b)      // sum of two double-floats (absolute accuracy)
+{
+    df s = df_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df dfa_f(df a, float b)
+{
+    df s = df_two_sum(a.hi, b);
+    s.lo += a.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_sqr(df a)
+{
+    df p = df_two_prod(a.hi, a.hi);
+    p.lo = fmaf(2.0f * a.hi, a.lo, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+
+// 1/sqrt(a) from y ~ rsqrtf(a.hi) by one Newton step with a double-float residual
+__device__ __forceinline__ df df_rsqrt(df a, float y)
+{
+    const df ay2 = df_mul(a, df_two_prod(y, y));   // ~ 1
+    const float e = (1.0f - ay2.hi) - ay2.lo;
+    return df_fast_two_sum(y, y * (0.5f * e));
+}
 
 template <int LMAX>
 __global__ void __launch_bounds__(256) k_hartree_moments(DevPlan P, HartreeDev H, long long n_pts, const double *n,
@@ -36,23 +109,32 @@ __global__ void __launch_bounds__(256) k_hartree_moments(DevPlan P, HartreeDev H
         const int a = H.owner[p];
         if (a < 0) continue;
         const int k = H.shell[p];
-        const double2 g = H.rgrid[a];
+        const HartreeRad g = H.rad[a];
         const double dx = P.px[p] - P.atom_xyz[3 * a], dy = P.py[p] - P.atom_xyz[3 * a + 1],
                      dz = P.pz[p] - P.atom_xyz[3 * a + 2];
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
         if (!(r > 0.0)) continue;
-        const double rk = g.x * exp(g.y * (double)k);
-        const double val = P.pw[p] / (rk * rk * rk * g.y) * n[p];
-        double Y[L];
-        real_ylm_all<LMAX>(dx / r, dy / r, dz / r, Y);
+        const double rk = g.r0 * exp(g.lnq * (double)k);
+        const double val = P.pw[p] / (rk * rk * rk * g.lnq) * n[p];
+        const double ir = 1.0 / r;
+        double A[L];
+        ylm_unnormalised<LMAX, double>(dx * ir, dy * ir, dz * ir, A);
         double *dst = rho + (H.rad_off[a] + k) * kL;
 #pragma unroll
-        for (int q = 0; q < L; q++) atomicAdd(dst + q, val * Y[q]);
+        for (int q = 0; q < L; q++) atomicAdd(dst + q, val * A[q]);
     }
 }
 
-// one thread per (atom, lm)
-__global__ void k_hartree_radial(HartreeDev H, int l_max, const double *rho, double *V, double *Q)
+__device__ __forceinline__ double ipow(double r, int n)      // r^n, 0 <= n <= 9
+{
+    double p = 1.0;
+    for (int i = 0; i < n; i++) p *= r;
+    return p;
+}
+
+// one thread per (atom, lm); the thread with lm = 0 also packs the atom's
+// record for the evaluation
+__global__ void __launch_bounds__(32) k_hartree_radial(DevPlan P, HartreeDev H, int l_max, HartreeTabs T)
 {
     const int L = (l_max + 1) * (l_max + 1);
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -60,141 +142,208 @@ __global__ void k_hartree_radial(HartreeDev H, int l_max, const double *rho, dou
     const int a = (int)(t / L), lm = (int)(t % L);
     int l = 0;
     while ((l + 1) * (l + 1) <= lm) l++;
-    const double2 g = H.rgrid[a];
-    const int n = H.nrad[a];
+    const HartreeRad g = H.rad[a];
+    const int n = g.nrad;
     const long long o = H.rad_off[a];
-    const double h = g.y;
-    auto rk = [&](int k) { return g.x * exp(h * (double)k); };
-    auto f = [&](int k) { const double r = rk(k); return rho[(o + k) * kL + lm] * pow(r, (double)(l + 3)); };
-    auto gg = [&](int k) { const double r = rk(k); return rho[(o + k) * kL + lm] * pow(r, (double)(2 - l)); };
-    // integral over interval [k, k+1] of the cubic through the nearest four samples
-    auto seg = [&](auto fn, int k) {
-        if (n < 4) return 0.5 * h * (fn(k) + fn(k + 1));
-        if (k == 0) return h * (9.0 * fn(0) + 19.0 * fn(1) - 5.0 * fn(2) + fn(3)) / 24.0;
-        if (k == n - 2) return h * (fn(n - 4) - 5.0 * fn(n - 3) + 19.0 * fn(n - 2) + 9.0 * fn(n - 1)) / 24.0;
-        return h * (-fn(k - 1) + 13.0 * fn(k) + 13.0 * fn(k + 1) - fn(k + 2)) / 24.0;
-    };
-    const double pref = 4.0 * 3.14159265358979323846 / (2.0 * l + 1.0);
-    // inner integrals, forward; V gets the inner part first
-    double iin = f(0) / (double)(l + 3);
+    const double h = g.lnq;
+    double *rho = T.rho + o * kL + lm, *F = T.F + o * kL + lm, *Vin = T.Vd + o * kL + lm;
+    auto rk = [&](int k) { return g.r0 * exp(h * (double)k); };
+    // the integrands per dx = dr / r: f = rho r^(l+3) (inner), g = rho r^(2-l) (outer, over rho)
     for (int k = 0; k < n; k++) {
-        if (k > 0) iin += seg(f, k - 1);
-        V[(o + k) * kL + lm] = pref * iin / pow(rk(k), (double)(l + 1));
+        const double r = rk(k), rr = rho[(long long)k * kL];
+        F[(long long)k * kL] = rr * ipow(r, l + 3);
+        rho[(long long)k * kL] = l <= 2 ? rr * ipow(r, 2 - l) : rr / ipow(r, l - 2);
     }
-    Q[(long long)a * kL + lm] = iin;
-    // outer integrals, backward
+    // integral over interval [k, k+1] of the cubic through the nearest four samples (n >= 4)
+    auto seg = [&](const double *fn, int k) {
+        auto v = [&](int j) { return fn[(long long)j * kL]; };
+        if (k == 0) return h * (9.0 * v(0) + 19.0 * v(1) - 5.0 * v(2) + v(3)) / 24.0;
+        if (k == n - 2) return h * (v(n - 4) - 5.0 * v(n - 3) + 19.0 * v(n - 2) + 9.0 * v(n - 1)) / 24.0;
+        return h * (-v(k - 1) + 13.0 * v(k) + 13.0 * v(k + 1) - v(k + 2)) / 24.0;
+    };
+    // 4 pi/(2l+1), times K_lm^2 for the two unnormalised harmonics (moment, evaluation)
+    const double pref = 4.0 * 3.14159265358979323846 / (2.0 * l + 1.0) * ylm_norm2(l, lm - l * l - l);
+    // inner integrals, forward: the inner part of V in FP64 scratch
+    double iin = F[0] / (double)(l + 3);
+    for (int k = 0; k < n; k++) {
+        if (k > 0) iin += seg(F, k - 1);
+        Vin[(long long)k * kL] = pref * iin / ipow(rk(k), l + 1);
+    }
+    if (lm == 0) {
+        const float *aa = P.atom_dd + 6 * a;
+        const df q = df_from_double(pref * iin);
+        T.rec[3 * a] = make_float4(aa[0], aa[1], aa[2], aa[3]);
+        T.rec[3 * a + 1] = make_float4(aa[4], aa[5], g.rmax2_hi, g.rmax2_lo);
+        T.rec[3 * a + 2] = make_float4(q.hi, q.lo, 0.f, 0.f);
+    } else {
+        T.Qf[(long long)a * kLf + lm - 1] = (float)(pref * iin);
+    }
+    // outer integrals, backward; V = inner + outer part, stored once
     double iout = 0.0;
     for (int k = n - 1; k >= 0; k--) {
-        if (k < n - 1) iout += seg(gg, k);
-        V[(o + k) * kL + lm] += pref * iout * pow(rk(k), (double)l);
+        if (k < n - 1) iout += seg(rho, k);
+        const double v = Vin[(long long)k * kL] + pref * iout * ipow(rk(k), l);
+        if (lm == 0) T.V0[o + k] = v;
+        else T.Vf[(o + k) * kLf + lm - 1] = (float)v;
     }
 }
 
 // CTA per batch, thread per point; the atoms of the batch's system
 template <int LMAX>
-__global__ void __launch_bounds__(128) k_hartree_eval(DevPlan P, HartreeDev H, const double *V, const double *Q,
-                                                      double *vh)
+__global__ void __launch_bounds__(128) k_hartree_eval(DevPlan P, HartreeDev H, HartreeTabs T, double *vh)
 {
     constexpr int L = (LMAX + 1) * (LMAX + 1);
     const DevBatch B = P.batches[blockIdx.x];
     const long long a0 = H.sys_atom0[B.sys], a1 = H.sys_atom0[B.sys + 1];
     for (int i = threadIdx.x; i < B.np; i += blockDim.x) {
         const long long p = B.pt0 + i;
-        const double px = P.px[p], py = P.py[p], pz = P.pz[p];
-        double acc = 0.0;
+        const float *pp = P.pts_dd + 6 * p;
+        const df px{pp[0], pp[1]}, py{pp[2], pp[3]}, pz{pp[4], pp[5]};
+        df acc{0.f, 0.f};
         for (long long a = a0; a < a1; a++) {
-            const double dx = px - P.atom_xyz[3 * a], dy = py - P.atom_xyz[3 * a + 1], dz = pz - P.atom_xyz[3 * a + 2];
-            const double d = sqrt(dx * dx + dy * dy + dz * dz);
-            double Y[L];
-            if (d > 1e-12) {
-                real_ylm_all<LMAX>(dx / d, dy / d, dz / d, Y);
-            } else {
+            const float4 r0 = T.rec[3 * a], r1 = T.rec[3 * a + 1];
+            const df dx = dfa(px, df{-r0.x, -r0.y}), dy = dfa(py, df{-r0.z, -r0.w}), dz = dfa(pz, df{-r1.x, -r1.y});
+            const df d2 = dfa(dfa(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+            const float ri = d2.hi > 0.f ? rsqrtf(d2.hi) : 0.f;
+            float A[L];
+            if constexpr (LMAX > 0) ylm_unnormalised<LMAX, float>(dx.hi * ri, dy.hi * ri, dz.hi * ri, A);
+            float part = 0.f;
+            if (d2.hi > r1.z || (d2.hi == r1.z && d2.lo >= r1.w)) {
+                // beyond the last shell: the exterior multipoles
+                const float4 r2 = T.rec[3 * a + 2];
+                acc = dfa(acc, df_mul(df{r2.x, r2.y}, df_rsqrt(d2, ri)));
+                if constexpr (LMAX > 0) {
+                    constexpr int NQ4 = (L - 1 + 3) / 4;
+                    float q[NQ4 * 4];
+                    const float4 *q4 = reinterpret_cast<const float4 *>(T.Qf + a * kLf);
 #pragma unroll
-                for (int q = 0; q < L; q++) Y[q] = 0.0;
-                Y[0] = 0.28209479177387814;
-            }
-            const double2 g = H.rgrid[a];
-            const int n = H.nrad[a];
-            const double r0 = g.x, rmax = g.x * exp(g.y * (double)(n - 1));
-            const double *Va = V + H.rad_off[a] * kL;
-            if (d >= rmax) {
-                // exterior multipole field
-                const double inv = 1.0 / d;
-                double dl = inv;                           // 1/d^(l+1)
+                    for (int j = 0; j < NQ4; j++) {
+                        const float4 u = q4[j];
+                        q[4 * j] = u.x;
+                        q[4 * j + 1] = u.y;
+                        q[4 * j + 2] = u.z;
+                        q[4 * j + 3] = u.w;
+                    }
+                    float rl = ri * ri;                              // 1/d^(l+1), l = 1
 #pragma unroll
-                for (int l = 0; l <= LMAX; l++) {
-                    const double pref = 4.0 * 3.14159265358979323846 / (2.0 * l + 1.0) * dl;
-                    for (int m = -l; m <= l; m++) acc += pref * Q[a * kL + l * l + l + m] * Y[l * l + l + m];
-                    dl *= inv;
+                    for (int l = 1; l <= LMAX; l++) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int m = -l; m <= l; m++) s = fmaf(q[l * l + l + m - 1], A[l * l + l + m], s);
+                        part = fmaf(s, rl, part);
+                        rl *= ri;
+                    }
                 }
-            } else if (d <= r0) {
-                const double s = d / r0;
-                double sl = 1.0;
-#pragma unroll
-                for (int l = 0; l <= LMAX; l++) {
-                    for (int m = -l; m <= l; m++) acc += Va[l * l + l + m] * sl * Y[l * l + l + m];
-                    sl *= s;
-                }
             } else {
-                const double x = log(d / r0) / g.y;
-                int i0 = (int)floor(x) - 1;
-                i0 = i0 < 0 ? 0 : (i0 > n - 4 ? n - 4 : i0);
-                const double t = x - (double)i0;
-                // Lagrange weights at nodes t = 0, 1, 2, 3
-                const double w0 = -(t - 1.0) * (t - 2.0) * (t - 3.0) / 6.0;
-                const double w1 = t * (t - 2.0) * (t - 3.0) / 2.0;
-                const double w2 = -t * (t - 1.0) * (t - 3.0) / 2.0;
-                const double w3 = t * (t - 1.0) * (t - 2.0) / 6.0;
-                const double *v0 = Va + (long long)i0 * kL;
+                const HartreeRad g = H.rad[a];
+                const long long o = H.rad_off[a];
+                const double dd2 = (double)d2.hi + (double)d2.lo;
+                const double *v0 = T.V0 + o;
+                if (dd2 <= g.r0 * g.r0) {
+                    // inside the first shell: V(r_0) (d / r_0)^l
+                    acc = dfa(acc, df_from_double(v0[0]));
+                    if constexpr (LMAX > 0) {
+                        const float sr = d2.hi * ri * g.inv_r0;
+                        const float *vf = T.Vf + o * kLf;
+                        float sl = sr;
 #pragma unroll
-                for (int q = 0; q < L; q++)
-                    acc += (w0 * v0[q] + w1 * v0[kL + q] + w2 * v0[2 * kL + q] + w3 * v0[3 * kL + q]) * Y[q];
+                        for (int l = 1; l <= LMAX; l++) {
+                            float s = 0.f;
+#pragma unroll
+                            for (int m = -l; m <= l; m++) s = fmaf(vf[l * l + l + m - 1], A[l * l + l + m], s);
+                            part = fmaf(s, sl, part);
+                            sl *= sr;
+                        }
+                    }
+                } else {
+                    const double x = (0.5 * log(dd2) - g.ln_r0) * g.inv_lnq;
+                    int i0 = (int)floor(x) - 1;
+                    i0 = i0 < 0 ? 0 : (i0 > g.nrad - 4 ? g.nrad - 4 : i0);
+                    const double t = x - (double)i0;
+                    // Lagrange weights at nodes t = 0, 1, 2, 3
+                    const double w0 = -(t - 1.0) * (t - 2.0) * (t - 3.0) * (1.0 / 6.0);
+                    const double w1 = t * (t - 2.0) * (t - 3.0) * 0.5;
+                    const double w2 = -t * (t - 1.0) * (t - 3.0) * 0.5;
+                    const double w3 = t * (t - 1.0) * (t - 2.0) * (1.0 / 6.0);
+                    acc = dfa(acc, df_from_double(w0 * v0[i0] + w1 * v0[i0 + 1] + w2 * v0[i0 + 2] + w3 * v0[i0 + 3]));
+                    if constexpr (LMAX > 0) {
+                        const float f0 = (float)w0, f1 = (float)w1, f2 = (float)w2, f3 = (float)w3;
+                        const float *vf = T.Vf + (o + i0) * kLf;
+#pragma unroll
+                        for (int q = 1; q < L; q++)
+                            part = fmaf(f0 * vf[q - 1] + f1 * vf[kLf + q - 1] + f2 * vf[2 * kLf + q - 1] +
+                                            f3 * vf[3 * kLf + q - 1],
+                                        A[q], part);
+                    }
+                }
             }
+            acc = dfa_f(acc, part);
         }
-        vh[p] = acc;
+        vh[p] = (double)acc.hi + (double)acc.lo;
     }
 }
 
 }  // namespace
 
+HartreeRad hartree_rad(double r_min, double ln_q, int n_rad)
+{
+    HartreeRad g{};
+    g.r0 = r_min;
+    g.lnq = ln_q;
+    g.inv_lnq = 1.0 / ln_q;
+    g.ln_r0 = std::log(r_min);
+    const double rmax = r_min * std::exp(ln_q * (double)(n_rad - 1));
+    const double r2 = rmax * rmax;
+    const df d = df_from_double(r2);
+    // a normalised pair: hi the nearest float, lo the remainder rounded
+    g.rmax2_hi = d.hi;
+    g.rmax2_lo = d.lo;
+    g.inv_r0 = (float)(1.0 / r_min);
+    g.nrad = n_rad;
+    return g;
+}
+
 size_t hartree_ws_bytes(const HartreeDev &H)
 {
-    return (size_t)(2 * H.n_shells + H.n_atoms) * kL * sizeof(double);
+    return 3 * al256(sizeof(double) * kL * (size_t)H.n_shells) + al256(sizeof(float4) * 3 * (size_t)H.n_atoms) +
+           al256(sizeof(double) * (size_t)H.n_shells) +
+           al256(sizeof(float) * kLf * (size_t)H.n_shells) +
+           al256(sizeof(float) * kLf * (size_t)H.n_atoms);
 }
 
 cudaError_t launch_hartree(const DevPlan &P, const HartreeDev &H, int n_batch, long long n_pts, int l_max,
                            const double *n, double *vh, double *ws, cudaStream_t s)
 {
-    double *rho = ws, *V = ws + H.n_shells * kL, *Q = ws + 2 * H.n_shells * kL;
-    cudaError_t e = cudaMemsetAsync(rho, 0, (size_t)H.n_shells * kL * sizeof(double), s);
+    const HartreeTabs T = carve(H, ws);
+    cudaError_t e = cudaMemsetAsync(T.rho, 0, sizeof(double) * kL * (size_t)H.n_shells, s);
     if (e != cudaSuccess) return e;
     if (n_pts > 0) {
         const unsigned grid = (unsigned)std::min<long long>((n_pts + 255) / 256, 4864);
         switch (l_max) {
-        case 0: k_hartree_moments<0><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        case 1: k_hartree_moments<1><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        case 2: k_hartree_moments<2><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        case 3: k_hartree_moments<3><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        case 4: k_hartree_moments<4><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        case 5: k_hartree_moments<5><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
-        default: k_hartree_moments<6><<<grid, 256, 0, s>>>(P, H, n_pts, n, rho); break;
+        case 0: k_hartree_moments<0><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        case 1: k_hartree_moments<1><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        case 2: k_hartree_moments<2><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        case 3: k_hartree_moments<3><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        case 4: k_hartree_moments<4><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        case 5: k_hartree_moments<5><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
+        default: k_hartree_moments<6><<<grid, 256, 0, s>>>(P, H, n_pts, n, T.rho); break;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const long long nt = (long long)H.n_atoms * (l_max + 1) * (l_max + 1);
     if (nt > 0) {
-        k_hartree_radial<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(H, l_max, rho, V, Q);
+        k_hartree_radial<<<(unsigned)((nt + 31) / 32), 32, 0, s>>>(P, H, l_max, T);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (n_batch > 0) {
         switch (l_max) {
-        case 0: k_hartree_eval<0><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        case 1: k_hartree_eval<1><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        case 2: k_hartree_eval<2><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        case 3: k_hartree_eval<3><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        case 4: k_hartree_eval<4><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        case 5: k_hartree_eval<5><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
-        default: k_hartree_eval<6><<<n_batch, 128, 0, s>>>(P, H, V, Q, vh); break;
+        case 0: k_hartree_eval<0><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        case 1: k_hartree_eval<1><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        case 2: k_hartree_eval<2><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        case 3: k_hartree_eval<3><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        case 4: k_hartree_eval<4><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        case 5: k_hartree_eval<5><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
+        default: k_hartree_eval<6><<<n_batch, 128, 0, s>>>(P, H, T, vh); break;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -9,17 +9,28 @@
 
 namespace fgi {
 
+// one atom's radial grid, with what the evaluation needs precomputed
+struct HartreeRad {
+    double r0, lnq;                      // r_k = r0 exp(k ln q)
+    double inv_lnq, ln_r0;
+    float rmax2_hi, rmax2_lo;            // (last shell radius)^2 as a double-float
+    float inv_r0;
+    int nrad;
+};
+
 // the grid's atom-centred structure on the device
 struct HartreeDev {
     const int *owner = nullptr;          // [n_pts] owner atom (global index, -1: none)
     const int *shell = nullptr;          // [n_pts] radial shell on the owner's grid
     const long long *rad_off = nullptr;  // [n_atoms + 1] first shell of each atom in the shell tables
-    const double2 *rgrid = nullptr;      // [n_atoms] (r_min, ln q): r_k = r_min exp(k ln q)
-    const int *nrad = nullptr;           // [n_atoms] shells per atom
+    const HartreeRad *rad = nullptr;     // [n_atoms]
     const long long *sys_atom0 = nullptr;  // [n_sys + 1] first atom of each system
     int n_atoms = 0;
     long long n_shells = 0;
 };
+
+// radial grid record of one atom (host)
+HartreeRad hartree_rad(double r_min, double ln_q, int n_rad);
 
 // scratch of one call: multipoles and potentials on the shells, exterior moments
 size_t hartree_ws_bytes(const HartreeDev &H);

@@ -1377,32 +1377,31 @@ int fgi_set_atom_grids(fgi_ctx *c, const int32_t *owner, const int32_t *shell, c
     c->hg_nrad.assign(n_rad, n_rad + n_at);
     std::vector<long long> rad_off(n_at + 1, 0);
     for (int a = 0; a < n_at; a++) rad_off[a + 1] = rad_off[a] + n_rad[a];
-    std::vector<double2> rgrid(n_at);
-    for (int a = 0; a < n_at; a++) rgrid[a] = make_double2(r_min[a], ln_q[a]);
+    std::vector<HartreeRad> rgrid(n_at);
+    for (int a = 0; a < n_at; a++) rgrid[a] = hartree_rad(r_min[a], ln_q[a], n_rad[a]);
     std::vector<long long> sys_atom0(c->atom_off.begin(), c->atom_off.end());
     c->hd.n_atoms = n_at;
     c->hd.n_shells = rad_off[n_at];
     if (c->device >= 0) {
         DeviceGuard g(c->device);
         const size_t s_own = align_up(4 * (size_t)c->n_pts + 4, 256), s_off = align_up(8 * (size_t)(n_at + 1), 256),
-                     s_rg = align_up(16 * (size_t)n_at + 16, 256), s_nr = align_up(4 * (size_t)n_at + 4, 256),
+                     s_rg = align_up(sizeof(HartreeRad) * (size_t)(n_at + 1), 256),
                      s_sys = align_up(8 * sys_atom0.size(), 256);
-        const size_t tot = 2 * s_own + s_off + s_rg + s_nr + s_sys;
+        const size_t tot = 2 * s_own + s_off + s_rg + s_sys;
         CUDA_TRY(c, cudaMalloc((void **)&c->d_hartree, tot));
         char *b = c->d_hartree;
         CUDA_TRY(c, cudaMemcpy(b, owner, 4 * (size_t)c->n_pts, cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(b + s_own, shell, 4 * (size_t)c->n_pts, cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(b + 2 * s_own, rad_off.data(), 8 * rad_off.size(), cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off, rgrid.data(), 16 * (size_t)n_at, cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off + s_rg, n_rad, 4 * (size_t)n_at, cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off + s_rg + s_nr, sys_atom0.data(), 8 * sys_atom0.size(),
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off, rgrid.data(), sizeof(HartreeRad) * (size_t)n_at,
+                               cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(b + 2 * s_own + s_off + s_rg, sys_atom0.data(), 8 * sys_atom0.size(),
                                cudaMemcpyHostToDevice));
         c->hd.owner = (const int *)b;
         c->hd.shell = (const int *)(b + s_own);
         c->hd.rad_off = (const long long *)(b + 2 * s_own);
-        c->hd.rgrid = (const double2 *)(b + 2 * s_own + s_off);
-        c->hd.nrad = (const int *)(b + 2 * s_own + s_off + s_rg);
-        c->hd.sys_atom0 = (const long long *)(b + 2 * s_own + s_off + s_rg + s_nr);
+        c->hd.rad = (const HartreeRad *)(b + 2 * s_own + s_off);
+        c->hd.sys_atom0 = (const long long *)(b + 2 * s_own + s_off + s_rg);
     }
     c->have_atom_grids = true;
     return FGI_OK;

@@ -9,8 +9,12 @@ oracle (oracle/hartree.py), through the C ABI.
 * a spherical Gaussian charge on one atom: the closed form q erf(sqrt(a) r)/r;
 * five molecules in one plan: no potential crosses between systems;
 * l_max beyond the supported 6 is refused.
-Both sides are FP64 in different summation orders: 1e-10 relative to the
-largest |v_H|.
+Tolerance: the l = 0 terms run in FP64 / double-float on both sides (other
+summation orders: 1e-10 of the largest |v_H|); the kernel takes the l >= 1
+terms in FP32, each the result of at most ~30 roundings of relative size
+2^-24 (four-node interpolation, FP32 harmonics, the sum over l and m), so it
+adds at most 2^-18 times the oracle's per-point sum of the magnitudes of the
+l >= 1 terms (oracle.hartree: l1_bound).
 """
 import math
 
@@ -27,6 +31,13 @@ from tests import helpers as T
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_L1 = 2.0 ** -18
+
+
+def check(vh, ref, bound):
+    err = np.abs(vh - ref)
+    lim = TOL * np.abs(ref).max() + TOL_L1 * bound
+    assert np.all(err <= lim), (float(np.max(err / lim)), float(err.max()), float(np.abs(ref).max()))
 
 
 @pytest.fixture(scope="module")
@@ -58,11 +69,11 @@ def test_water_occupied_density(fgi, l_max):
     B = O.system_basis(prob)
     D, _ = W.density_matrix_occ(B.n_fn, 5, np.random.default_rng(3))
     n = O.density(B, prob.pts, D)
-    ref = OH.hartree(prob, n, l_max=l_max)
+    ref, bound = OH.hartree(prob, n, l_max=l_max, l1_bound=True)
     ctx = fgi.Context(0).load(prob, "fp64")
     vh = ctx.hartree(dev(n), l_max=l_max).cpu().numpy()
     ctx.sync()
-    assert np.max(np.abs(vh - ref)) <= TOL * np.abs(ref).max()
+    check(vh, ref, bound)
 
 
 def test_si64_gaussian_charges_sampled(fgi):
@@ -72,8 +83,8 @@ def test_si64_gaussian_charges_sampled(fgi):
     vh = ctx.hartree(dev(n), l_max=4).cpu().numpy()
     ctx.sync()
     idx = np.sort(np.random.default_rng(61).choice(prob.n_pts, 1500, replace=False))
-    ref = OH.hartree(prob, n, l_max=4, pts_idx=idx)
-    assert np.max(np.abs(vh[idx] - ref)) <= TOL * np.abs(ref).max()
+    ref, bound = OH.hartree(prob, n, l_max=4, pts_idx=idx, l1_bound=True)
+    check(vh[idx], ref, bound)
 
 
 def test_spherical_gaussian_closed_form(fgi):
@@ -94,14 +105,14 @@ def test_molecules_do_not_interact(fgi):
     ctx = fgi.Context(0).load(prob, "split_bf16")
     vh = ctx.hartree(dev(n), l_max=4).cpu().numpy()
     ctx.sync()
-    ref = OH.hartree(prob, n, l_max=4)
-    assert np.max(np.abs(vh - ref)) <= TOL * np.abs(ref).max()
+    ref, bound = OH.hartree(prob, n, l_max=4, l1_bound=True)
+    check(vh, ref, bound)
     # each molecule alone gives the same potential on its own points
     s = 2
     one = prob.system_problem(s)
     pts = prob.system_points(s)
-    alone = OH.hartree(one, n[pts], l_max=4)
-    assert np.max(np.abs(vh[pts] - alone)) <= TOL * np.abs(alone).max()
+    alone, bound1 = OH.hartree(one, n[pts], l_max=4, l1_bound=True)
+    check(vh[pts], alone, bound1)
 
 
 def test_l_max_beyond_six_is_refused(fgi):
