@@ -91,9 +91,12 @@ class HartreeTables:
         xyz = problem.atom_xyz
         self.V, self.Q, self.r, self.lnq, self.rho = [], [], [], [], []
         ls = np.concatenate([[l] * (2 * l + 1) for l in range(l_max + 1)]).astype(np.float64)
+        # the points of each owner atom (grouped once)
+        by_owner = np.argsort(problem.owner, kind="stable")
+        first = np.searchsorted(problem.owner[by_owner], np.arange(len(xyz) + 1))
         for a in range(len(xyz)):
             r_k, ln_q = _radii(problem.atom_rgrid[a])
-            sel = np.nonzero(problem.owner == a)[0]
+            sel = by_owner[first[a]:first[a + 1]]
             rho = np.zeros((len(r_k), L))
             if len(sel):
                 dvec = problem.pts[sel] - xyz[a][None, :]

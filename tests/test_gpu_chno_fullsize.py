@@ -7,14 +7,18 @@ cutoffs (the others contribute exactly zero), and the density at every
 point of a dozen seeded batches, with D = 2 C_occ C_occ^T drawn as the
 benchmark draws it.  A property that holds at any size (split BF16 within
 the stated tolerance of the FP64 GPU path on every stored entry and every
-point) covers the rest.  Marked slow: the FP64 path alone takes most of a
-minute on this cluster.
+point) covers the rest.  The Hartree potential of a seeded synthetic
+density (owner-centred Gaussians with point-to-point noise) is checked at
+seeded sample points against the oracle (multipoles of every atom).  Marked
+slow: the FP64 path alone takes most of a minute on this cluster, the
+oracle's Hartree multipoles a few minutes.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
+import oracle.hartree as OH
 import workloads as W
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -45,9 +49,14 @@ def chno_full():
     ns = ctx.density(d)[0].cpu().numpy()
     ctx.set_precision("fp64")
     n64 = ctx.density(d)[0].cpu().numpy()
+    # Hartree input: Z exp(-1.1 d^2) of the owning atom, times 1 + 0.3 u (seeded)
+    Z = np.array([prob.species[int(s)].Z for s in prob.atom_species], dtype=np.float64)
+    dist2 = np.sum((prob.pts - prob.atom_xyz[prob.owner]) ** 2, axis=1)
+    n_h = Z[prob.owner] * np.exp(-1.1 * dist2) * (1.0 + 0.3 * np.random.default_rng(43).random(prob.n_pts))
+    vh = ctx.hartree(torch.from_numpy(n_h).cuda(), l_max=4).cpu().numpy()
     ctx.sync()
     ctx.close()
-    return dict(prob=prob, rows=rows, col=col, h64=h64, hs=hs, ns=ns, n64=n64, q=q)
+    return dict(prob=prob, rows=rows, col=col, h64=h64, hs=hs, ns=ns, n64=n64, q=q, n_h=n_h, vh=vh)
 
 
 def test_full_h_sampled_entries_against_oracle(chno_full):
@@ -89,3 +98,13 @@ def test_full_split_within_tolerance_on_every_entry(chno_full):
     f = chno_full
     assert np.max(np.abs(f["hs"] - f["h64"])) <= TOL_SPLIT_H
     assert np.linalg.norm(f["ns"] - f["n64"]) / np.linalg.norm(f["n64"]) <= TOL_SPLIT_N
+
+
+def test_full_hartree_sampled_points_against_oracle(chno_full):
+    """Tolerance as in test_gpu_hartree: 1e-10 of max |v_H| plus 2^-18 of
+    the per-point scale of the FP32 l >= 1 terms."""
+    f = chno_full
+    idx = np.sort(np.random.default_rng(44).choice(f["prob"].n_pts, 200, replace=False))
+    ref, bound = OH.hartree(f["prob"], f["n_h"], l_max=4, pts_idx=idx, l1_bound=True)
+    err = np.abs(f["vh"][idx] - ref)
+    assert np.all(err <= 1e-10 * np.abs(ref).max() + 2.0 ** -18 * bound), float(err.max())
