@@ -287,9 +287,15 @@ int fgi_hartree_workspace_size(fgi_ctx *ctx, size_t *bytes);
         interpolation in the fractional shell index, 4 pi/(2l+1) Q_lm /
         d^(l+1) beyond the last shell, V(r_0) (d/r_0)^l inside the first.
    n_dev, vh_dev: device [n_pts] FP64 in the caller's point order;
-   0 <= l_max <= 6 (FGI_ERR_UNSUPPORTED otherwise).  FP64 throughout; the
-   evaluation visits every (point, atom) pair of a system.  Needs a plan and
-   fgi_set_atom_grids. */
+   0 <= l_max <= 6 (FGI_ERR_UNSUPPORTED otherwise).  Moments and the radial
+   solve in FP64; the evaluation (every (point, atom) pair of a system) takes
+   the l = 0 terms as double-floats (~1e-12 relative; FP64 interpolation for
+   radial grids with ln q > 0.6) and the l >= 1 terms in FP32 (a few FP32
+   roundings of the l >= 1 part).  The moments are summed with FP64 atomics:
+   not bitwise reproducible.  Needs a plan and fgi_set_atom_grids;
+   ws: device, 256-byte aligned, at least fgi_hartree_workspace_size bytes
+   (FGI_ERR_WORKSPACE otherwise).  Enqueued on stream, no allocation, no host
+   synchronisation (graph-capturable). */
 int fgi_hartree(fgi_ctx *ctx, const double *n_dev, double *vh_dev, int l_max, void *ws, size_t ws_bytes,
                 void *stream);
 

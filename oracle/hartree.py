@@ -124,9 +124,11 @@ class HartreeTables:
 
     def radial(self, a: int, d: np.ndarray, magnitude: bool = False) -> np.ndarray:
         """V_a,lm at distances d [n]: (n, L).  magnitude: instead the size of
-        what is summed for each entry (|V| beyond and inside the grid, the sum
-        of |weight x V| over the four interpolation nodes between shells), the
-        scale of the rounding error of any evaluation of it."""
+        what is summed for each entry (|V| beyond and inside the grid; between
+        shells the sum over the four interpolation nodes of
+        (|weight| + |t d weight/dt|) |V|, the second part the first-order
+        effect of a relative rounding of t itself), the scale of the rounding
+        error of any evaluation of it."""
         V, r_k, ln_q = self.V[a], self.r[a], self.lnq[a]
         n_rad = len(r_k)
         out = np.empty((len(d), V.shape[1]))
@@ -150,8 +152,19 @@ class HartreeTables:
                 for m in range(4):
                     if m != j:
                         lj *= (t - m) / (j - m)
-                term = lj[:, None] * V[i0 + j]
-                acc += np.abs(term) if magnitude else term
+                if magnitude:
+                    dl = np.zeros_like(t)                # d l_j / dt
+                    for m in range(4):
+                        if m == j:
+                            continue
+                        pm = np.ones_like(t) / (j - m)
+                        for q in range(4):
+                            if q != j and q != m:
+                                pm *= (t - q) / (j - q)
+                        dl += pm
+                    acc += (np.abs(lj) + np.abs(t * dl))[:, None] * np.abs(V[i0 + j])
+                else:
+                    acc += lj[:, None] * V[i0 + j]
             out[mid] = acc
         return out
 

@@ -19,7 +19,9 @@
 //     l >= 1 in FP32.
 //  3. k_hartree_eval: per point, over the atoms of its system, V_a,lm at the
 //     distance times Y_lm of the direction: 4-point Lagrange interpolation in
-//     the fractional shell index inside the grid (l = 0 in FP64),
+//     the fractional shell index inside the grid (l = 0 as a double-float:
+//     the interpolating cubic of each interval stored in f = x - k, and
+//     f = ln(d / r_k) / ln q from an atanh series; FP64 for coarse grids),
 //     4 pi/(2l+1) Q_lm / d^(l+1) beyond the last shell (l = 0 as a
 //     double-float: offset, distance and 1/d from the double-float point and
 //     atom positions), V(r_0) (d/r_0)^l inside the first shell.  The l >= 1
@@ -37,12 +39,17 @@ namespace {
 
 constexpr int kL = (kHartreeLmax + 1) * (kHartreeLmax + 1);  // stride of the FP64 moment rows
 constexpr int kLf = kL - 1;                                     // stride of the FP32 l >= 1 rows
+// 2/3 and 2/5 as double-floats (compile-time)
+constexpr float kTwoThirdHi = (float)(2.0 / 3.0), kTwoThirdLo = (float)(2.0 / 3.0 - (double)kTwoThirdHi);
+constexpr float kTwoFifthHi = (float)(2.0 / 5.0), kTwoFifthLo = (float)(2.0 / 5.0 - (double)kTwoFifthHi);
 
 struct HartreeTabs {
     double *rho;      // [n_shells][kL]    unnormalised moments
     double *Vd;       // [n_shells][kL]    scratch: inner part of V
     double *F;        // [n_shells][kL]    scratch: inner integrand
     float4 *rec;      // [n_atoms][3]      position (double-float), (last radius)^2, 4 pi K_00^2 Q_00
+    float4 *rk;       // [n_shells]        r_k and 1/r_k as double-floats
+    float4 *c0;       // [n_shells][2]     V_00 on interval k as a cubic in f (double-floats a0..a3)
     double *V0;       // [n_shells]        K_00^2 V_00
     float *Vf;        // [n_shells][kLf]   K_lm^2 V_lm, l >= 1
     float *Qf;        // [n_atoms][kLf]    4 pi/(2l+1) K_lm^2 Q_lm, l >= 1
@@ -62,6 +69,10 @@ HartreeTabs carve(const HartreeDev &H, void *ws)
     b += al256(sizeof(double) * kL * (size_t)H.n_shells);
     T.rec = (float4 *)b;
     b += al256(sizeof(float4) * 3 * (size_t)H.n_atoms);
+    T.rk = (float4 *)b;
+    b += al256(sizeof(float4) * (size_t)H.n_shells);
+    T.c0 = (float4 *)b;
+    b += al256(sizeof(float4) * 2 * (size_t)H.n_shells);
     T.V0 = (double *)b;
     b += al256(sizeof(double) * (size_t)H.n_shells);
     T.Vf = (float *)b;
@@ -186,6 +197,28 @@ __global__ void __launch_bounds__(32) k_hartree_radial(DevPlan P, HartreeDev H, 
         if (lm == 0) T.V0[o + k] = v;
         else T.Vf[(o + k) * kLf + lm - 1] = (float)v;
     }
+    if (lm != 0) return;
+    // the shells' radii, and V_00 on each interval k as the cubic through
+    // shells i0 .. i0+3 (i0 = k - 1 clamped to [0, n-4]) in f = x - k,
+    // x = ln(r / r_0) / ln q: a_m = p^(m)(o) / m! with o = k - i0 and
+    // p(t) = V_i0 + t D1 + t(t-1)/2 D2 + t(t-1)(t-2)/6 D3 (forward differences)
+    for (int k = 0; k < n; k++) {
+        const double r = rk(k);
+        const df rh = df_from_double(r), ri = df_from_double(1.0 / r);
+        T.rk[o + k] = make_float4(rh.hi, rh.lo, ri.hi, ri.lo);
+    }
+    for (int k = 0; k + 1 < n; k++) {
+        const int i0 = k - 1 < 0 ? 0 : (k - 1 > n - 4 ? n - 4 : k - 1);
+        const double t = (double)(k - i0);
+        const double *v = T.V0 + o + i0;
+        const double D1 = v[1] - v[0], D2 = v[2] - 2.0 * v[1] + v[0], D3 = v[3] - 3.0 * v[2] + 3.0 * v[1] - v[0];
+        const df a0 = df_from_double(v[k - i0]);
+        const df a1 = df_from_double(D1 + (2.0 * t - 1.0) * 0.5 * D2 + (3.0 * t * t - 6.0 * t + 2.0) * (1.0 / 6.0) * D3);
+        const df a2 = df_from_double(0.5 * (D2 + (t - 1.0) * D3));
+        const df a3 = df_from_double(D3 * (1.0 / 6.0));
+        T.c0[2 * (o + k)] = make_float4(a0.hi, a0.lo, a1.hi, a1.lo);
+        T.c0[2 * (o + k) + 1] = make_float4(a2.hi, a2.lo, a3.hi, a3.lo);
+    }
 }
 
 // CTA per batch, thread per point; the atoms of the batch's system
@@ -237,11 +270,11 @@ __global__ void __launch_bounds__(128) k_hartree_eval(DevPlan P, HartreeDev H, H
             } else {
                 const HartreeRad g = H.rad[a];
                 const long long o = H.rad_off[a];
-                const double dd2 = (double)d2.hi + (double)d2.lo;
-                const double *v0 = T.V0 + o;
-                if (dd2 <= g.r0 * g.r0) {
+                const float4 R0 = T.rk[o];
+                const df r02 = df_sqr(df{R0.x, R0.y});
+                if (d2.hi < r02.hi || (d2.hi == r02.hi && d2.lo <= r02.lo)) {
                     // inside the first shell: V(r_0) (d / r_0)^l
-                    acc = dfa(acc, df_from_double(v0[0]));
+                    acc = dfa(acc, df_from_double(T.V0[o]));
                     if constexpr (LMAX > 0) {
                         const float sr = d2.hi * ri * g.inv_r0;
                         const float *vf = T.Vf + o * kLf;
@@ -256,18 +289,77 @@ __global__ void __launch_bounds__(128) k_hartree_eval(DevPlan P, HartreeDev H, H
                         }
                     }
                 } else {
-                    const double x = (0.5 * log(dd2) - g.ln_r0) * g.inv_lnq;
-                    int i0 = (int)floor(x) - 1;
-                    i0 = i0 < 0 ? 0 : (i0 > g.nrad - 4 ? g.nrad - 4 : i0);
-                    const double t = x - (double)i0;
-                    // Lagrange weights at nodes t = 0, 1, 2, 3
-                    const double w0 = -(t - 1.0) * (t - 2.0) * (t - 3.0) * (1.0 / 6.0);
-                    const double w1 = t * (t - 2.0) * (t - 3.0) * 0.5;
-                    const double w2 = -t * (t - 1.0) * (t - 3.0) * 0.5;
-                    const double w3 = t * (t - 1.0) * (t - 2.0) * (1.0 / 6.0);
-                    acc = dfa(acc, df_from_double(w0 * v0[i0] + w1 * v0[i0 + 1] + w2 * v0[i0 + 2] + w3 * v0[i0 + 3]));
+                    // between shells: interval k (r_k <= d < r_k+1), f = ln(d / r_k) / ln q
+                    int k, i0;
+                    float t;
+                    if (g.df_log) {
+                        // double-float: k from an FP32 estimate of x = ln(d / r_0) / ln q,
+                        // corrected against the radii; ln(d / r_k) = 2 atanh(s),
+                        // s = u / (2 + u), u = d / r_k - 1 < q - 1:
+                        // 2 s + s z (2/3 + z (2/5 + z R(z))), z = s^2, with the terms
+                        // to s^5 as double-floats and R = 2/7 + 2/9 z + ... + 2/19 z^6
+                        // in FP32 (ln q <= 0.6 keeps s <= 0.3; the FP32 part's rounding
+                        // and the first dropped term, 2 s^21 / 21, together stay below
+                        // 6e-12 in ln(d / r_k))
+                        const df d = df_sqrt(d2);
+                        k = (int)floorf((__logf(d.hi) - g.ln_r0_f) * g.inv_lnq_f);
+                        k = k < 0 ? 0 : (k > g.nrad - 2 ? g.nrad - 2 : k);
+                        float4 Rk = T.rk[o + k];
+                        if (k > 0 && (d.hi < Rk.x || (d.hi == Rk.x && d.lo < Rk.y))) {
+                            k--;
+                            Rk = T.rk[o + k];
+                        } else if (k < g.nrad - 2) {
+                            const float4 R1 = T.rk[o + k + 1];
+                            if (!(d.hi < R1.x || (d.hi == R1.x && d.lo < R1.y))) {
+                                k++;
+                                Rk = R1;
+                            }
+                        }
+                        const df u = dfa(df_mul(d, df{Rk.z, Rk.w}), df{-1.f, 0.f});
+                        const df sv = df_mul(u, df_rcp(dfa(u, df{2.f, 0.f})));
+                        const df z = df_sqr(sv);
+                        float rz = 2.f / 19.f;
+                        rz = fmaf(rz, z.hi, 2.f / 17.f);
+                        rz = fmaf(rz, z.hi, 2.f / 15.f);
+                        rz = fmaf(rz, z.hi, 2.f / 13.f);
+                        rz = fmaf(rz, z.hi, 2.f / 11.f);
+                        rz = fmaf(rz, z.hi, 2.f / 9.f);
+                        rz = fmaf(rz, z.hi, 2.f / 7.f);
+                        df ser = dfa_f(df{kTwoFifthHi, kTwoFifthLo}, z.hi * rz);     // 2/5 + z R
+                        ser = dfa(df{kTwoThirdHi, kTwoThirdLo}, df_mul(z, ser));     // 2/3 + z (...)
+                        const df ln1p = dfa(df{2.f * sv.hi, 2.f * sv.lo}, df_mul(sv, df_mul(z, ser)));
+                        const df f = df_mul(ln1p, df{g.inv_lnq_hi, g.inv_lnq_lo});
+                        // V_00 = a0 + f (a1 + f (a2 + f a3)) on interval k
+                        const float4 c01 = T.c0[2 * (o + k)], c23 = T.c0[2 * (o + k) + 1];
+                        df pv = dfa(df{c23.x, c23.y}, df_mul(f, df{c23.z, c23.w}));
+                        pv = dfa(df{c01.z, c01.w}, df_mul(f, pv));
+                        pv = dfa(df{c01.x, c01.y}, df_mul(f, pv));
+                        acc = dfa(acc, pv);
+                        i0 = k - 1 < 0 ? 0 : (k - 1 > g.nrad - 4 ? g.nrad - 4 : k - 1);
+                        t = (float)(k - i0) + f.hi;
+                    } else {
+                        // coarse radial grids: FP64 logarithm and Lagrange weights
+                        const double dd2 = (double)d2.hi + (double)d2.lo;
+                        const double *v0 = T.V0 + o;
+                        const double x = (0.5 * log(dd2) - g.ln_r0) * g.inv_lnq;
+                        i0 = (int)floor(x) - 1;
+                        i0 = i0 < 0 ? 0 : (i0 > g.nrad - 4 ? g.nrad - 4 : i0);
+                        const double td = x - (double)i0;
+                        const double w0 = -(td - 1.0) * (td - 2.0) * (td - 3.0) * (1.0 / 6.0);
+                        const double w1 = td * (td - 2.0) * (td - 3.0) * 0.5;
+                        const double w2 = -td * (td - 1.0) * (td - 3.0) * 0.5;
+                        const double w3 = td * (td - 1.0) * (td - 2.0) * (1.0 / 6.0);
+                        acc = dfa(acc, df_from_double(w0 * v0[i0] + w1 * v0[i0 + 1] + w2 * v0[i0 + 2] + w3 * v0[i0 + 3]));
+                        t = (float)td;
+                        k = 0;
+                    }
+                    (void)k;
                     if constexpr (LMAX > 0) {
-                        const float f0 = (float)w0, f1 = (float)w1, f2 = (float)w2, f3 = (float)w3;
+                        // l >= 1: Lagrange weights at nodes t = 0, 1, 2, 3 (shells i0 .. i0+3), FP32
+                        const float f0 = -(t - 1.f) * (t - 2.f) * (t - 3.f) * (1.f / 6.f);
+                        const float f1 = t * (t - 2.f) * (t - 3.f) * 0.5f;
+                        const float f2 = -t * (t - 1.f) * (t - 3.f) * 0.5f;
+                        const float f3 = t * (t - 1.f) * (t - 2.f) * (1.f / 6.f);
                         const float *vf = T.Vf + (o + i0) * kLf;
 #pragma unroll
                         for (int q = 1; q < L; q++)
@@ -300,12 +392,19 @@ HartreeRad hartree_rad(double r_min, double ln_q, int n_rad)
     g.rmax2_lo = d.lo;
     g.inv_r0 = (float)(1.0 / r_min);
     g.nrad = n_rad;
+    const df il = df_from_double(1.0 / ln_q);
+    g.inv_lnq_hi = il.hi;
+    g.inv_lnq_lo = il.lo;
+    g.ln_r0_f = (float)std::log(r_min);
+    g.inv_lnq_f = (float)(1.0 / ln_q);
+    g.df_log = ln_q <= 0.6 ? 1 : 0;
     return g;
 }
 
 size_t hartree_ws_bytes(const HartreeDev &H)
 {
     return 3 * al256(sizeof(double) * kL * (size_t)H.n_shells) + al256(sizeof(float4) * 3 * (size_t)H.n_atoms) +
+           al256(sizeof(float4) * (size_t)H.n_shells) + al256(sizeof(float4) * 2 * (size_t)H.n_shells) +
            al256(sizeof(double) * (size_t)H.n_shells) +
            al256(sizeof(float) * kLf * (size_t)H.n_shells) +
            al256(sizeof(float) * kLf * (size_t)H.n_atoms);

@@ -16,6 +16,10 @@ struct HartreeRad {
     float rmax2_hi, rmax2_lo;            // (last shell radius)^2 as a double-float
     float inv_r0;
     int nrad;
+    float inv_lnq_hi, inv_lnq_lo;        // 1/ln q as a double-float
+    float ln_r0_f, inv_lnq_f;            // FP32 copies for the interval estimate
+    int df_log;                          // ln q small enough for the double-float logarithm
+    int pad[3];
 };
 
 // the grid's atom-centred structure on the device

@@ -121,3 +121,61 @@ def test_l_max_beyond_six_is_refused(fgi):
     with pytest.raises(fgi.FGIError) as e:
         ctx.hartree(dev(np.zeros(prob.n_pts)), l_max=7)
     assert e.value.code == -7
+
+
+def test_degenerate_points_and_zero_density(fgi):
+    """Points without an owner (they contribute nothing and still get v_H), a
+    point exactly on a nucleus (d = 0: the l = 0 limit inside the first
+    shell), the minimal four-shell radial grids, and n = 0 (v_H = 0 exactly)."""
+    centers = [[0.0, 0.0, 0.0], [1.4, -0.6, 0.9]]
+    prob = T.gaussian_problem(centers, [[(0, 1.0)], [(1, 0.8)]], n_rad=4, n_ang=26, p_max=30, p_min=5,
+                              r_cut=6.0)
+    rng = np.random.default_rng(17)
+    orphan = rng.choice(prob.n_pts, prob.n_pts // 10, replace=False)
+    prob.owner = prob.owner.copy()
+    prob.owner[orphan] = -1
+    j = int(orphan[0])
+    prob.pts = prob.pts.copy()
+    prob.pts[j] = prob.atom_xyz[1]
+    n = gaussians(prob, alpha=0.7) * (1.0 + 0.5 * rng.random(prob.n_pts))
+    ref, bound = OH.hartree(prob, n, l_max=2, l1_bound=True)
+    ctx = fgi.Context(0).load(prob, "fp64")
+    vh = ctx.hartree(dev(n), l_max=2).cpu().numpy()
+    zero = ctx.hartree(dev(np.zeros(prob.n_pts)), l_max=2).cpu().numpy()
+    ctx.sync()
+    check(vh, ref, bound)
+    assert np.all(zero == 0.0)
+
+
+@pytest.mark.parametrize("l_max", [0, 1, 2, 3, 5])
+def test_every_l_max(fgi, l_max):
+    prob = W.tiny_water(n_rad=20, n_ang=50)
+    n = gaussians(prob, alpha=0.9) * (1.0 + 0.4 * np.random.default_rng(5).random(prob.n_pts))
+    ref, bound = OH.hartree(prob, n, l_max=l_max, l1_bound=True)
+    ctx = fgi.Context(0).load(prob, "split_bf16")
+    vh = ctx.hartree(dev(n), l_max=l_max).cpu().numpy()
+    ctx.sync()
+    check(vh, ref, bound)
+
+
+def test_hartree_replays_as_a_cuda_graph(fgi):
+    """fgi_hartree allocates nothing and never waits on the host: captured
+    once, a replay with a new density in the same buffer equals a direct call
+    to rounding (the moments are summed with FP64 atomics, in no fixed
+    order, so the two agree to about 1e-15, not bitwise)."""
+    prob = W.tiny_water(n_rad=20, n_ang=50)
+    ctx = fgi.Context(0).load(prob, "split_bf16")
+    n_buf = dev(gaussians(prob))
+    vh = ctx.hartree(n_buf, l_max=4)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.hartree(n_buf, l_max=4, vh=vh, stream=s)
+    n2 = gaussians(prob, alpha=0.6)
+    n_buf.copy_(dev(n2))
+    g.replay()
+    torch.cuda.synchronize()
+    direct = ctx.hartree(dev(n2), l_max=4).cpu().numpy()
+    ctx.sync()
+    np.testing.assert_allclose(vh.cpu().numpy(), direct, rtol=0, atol=1e-13 * np.abs(direct).max())
