@@ -47,6 +47,18 @@ __device__ __forceinline__ df df_add(df a, df b)
 
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df{-b.hi, -b.lo}); }
 
+// Sum with one error-free transformation (the high parts) and a rounded sum
+// of the low parts: error within about 2^-48 (|a| + |b|) instead of
+// 2^-48 |a + b|.  Exact enough for sums of one sign, and for differences of
+// grid coordinates, whose rounding differs from point to point.
+__device__ __forceinline__ df df_add_sloppy(df a, df b)
+{
+    const df s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df df_sub_sloppy(df a, df b) { return df_add_sloppy(a, df{-b.hi, -b.lo}); }
+
 __device__ __forceinline__ df df_mul(df a, df b)
 {
     df p = df_two_prod(a.hi, b.hi);
@@ -78,6 +90,29 @@ __device__ __forceinline__ df df_rcp(df a)
     e = fmaf(-a.lo, r, e);
     return df_fast_two_sum(r, e * r);
 }
+
+// 1/sqrt(a) from an approximation y (relative error up to ~2^-20): with
+// rho = 1 - a y^2 (from exact products, to about 2^-46 absolute),
+// 1/sqrt(a) = y (1 - rho)^(-1/2) = y (1 + rho/2 + 3 rho^2/8 + O(rho^3)).
+// Host-callable so that tests can check it against FP64 with a perturbed y.
+__host__ __device__ __forceinline__ df df_rsqrt_refine(df a, float y)
+{
+    const float y2h = y * y;
+    const float y2l = fmaf(y, y, -y2h);
+    const float ph = a.hi * y2h;
+    const float pl = fmaf(a.hi, y2h, -ph);
+    // 1 - ph is exact (ph is within a factor two of 1)
+    const float rho = ((1.f - ph) - pl) - fmaf(a.hi, y2l, a.lo * y2h);
+    const float c = y * (rho * fmaf(0.375f, rho, 0.5f));
+    const float s = y + c;
+    return {s, c - (s - y)};
+}
+
+#if defined(__CUDACC__)
+// 1/sqrt(a) for a > 0 (a.hi a normal FP32 number): the FP32 approximation
+// rsqrtf refined once
+__device__ __forceinline__ df df_rsqrt(df a) { return df_rsqrt_refine(a, rsqrtf(a.hi)); }
+#endif
 
 __host__ __device__ __forceinline__ df df_from_double(double x)
 {

@@ -587,6 +587,24 @@ int build_plan(fgi_ctx *c, const char *tune_path)
             coef_dd[8 * k + q] = hi;
             coef_dd[8 * k + 4 + q] = (float)(coef[4 * k + q] - (double)hi);
         }
+    // the same with every coefficient times the first normalisation constant
+    // of the radial's l (real harmonics, no Condon-Shortley phase): the
+    // lane-per-point basis kernels evaluate C_l u(r) directly
+    static const double kFirstYlmC[4] = {0.28209479177387814,   // 1/(2 sqrt pi)
+                                         0.4886025119029199,    // sqrt(3/(4 pi))
+                                         1.0925484305920792,    // (1/2) sqrt(15/pi), xy
+                                         0.5900435899266435};   // (1/4) sqrt(35/(2 pi)), y(3x^2 - y^2)
+    std::vector<float> coef_ddn(coef.size() * 2);
+    for (size_t i = 0; i < c->radials.size(); i++) {
+        const double cl = kFirstYlmC[std::min(std::max(c->radials[i].l, 0), 3)];
+        for (long long k = drad[i].coef_off; k < drad[i].coef_off + (long long)(c->radials[i].coef.size() / 4); k++)
+            for (int q = 0; q < 4; q++) {
+                const double v = coef[4 * k + q] * cl;
+                const float hi = (float)v;
+                coef_ddn[8 * k + q] = hi;
+                coef_ddn[8 * k + 4 + q] = (float)(v - (double)hi);
+            }
+    }
     // coordinates as double-floats: per point (x_hi, x_lo, y_hi, y_lo, z_hi, z_lo)
     auto to_dd = [](const double *xyz, int64_t n) {
         BigVec<float> out(6 * (size_t)n);
@@ -606,7 +624,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     // species whose shells share one knot grid also get their coefficients
     // interleaved by interval, so that one point's shells read neighbouring
     // cache lines
-    std::vector<float> scoef;
+    std::vector<float> scoef, scoefn;
+    std::vector<int> shell_fn0;
     for (const SpeciesH &s : c->species) {
         DevSpecies d{};
         d.shell0 = (int)shell_rad.size();
@@ -628,16 +647,22 @@ int build_plan(fgi_ctx *c, const char *tune_path)
                 for (int sh : s.shells) {
                     const size_t src = 8 * ((size_t)drad[sh].coef_off + k);
                     scoef.insert(scoef.end(), coef_dd.begin() + src, coef_dd.begin() + src + 8);
+                    scoefn.insert(scoefn.end(), coef_ddn.begin() + src, coef_ddn.begin() + src + 8);
                 }
         }
         shell_rad.insert(shell_rad.end(), s.shells.begin(), s.shells.end());
+        int fn = 0;
+        for (int sh : s.shells) {
+            shell_fn0.push_back(fn);
+            fn += 2 * c->radials[sh].l + 1;
+        }
         d.lmax = 0;
         for (int sh : s.shells) d.lmax = std::max(d.lmax, c->radials[sh].l);
         dsp.push_back(d);
     }
     std::vector<DevShell> dshell;
-    for (int r : shell_rad) {
-        const DevRadial &R = drad[r];
+    for (size_t i = 0; i < shell_rad.size(); i++) {
+        const DevRadial &R = drad[shell_rad[i]];
         DevShell q{};
         q.coef_off = (int)R.coef_off;
         q.nk = R.nk;
@@ -646,9 +671,11 @@ int build_plan(fgi_ctx *c, const char *tune_path)
         q.inv_h_hi = R.inv_h_hi;
         q.inv_h_lo = R.inv_h_lo;
         q.bound_off = (int)R.bound_off;
+        q.fn0 = shell_fn0[i];
         dshell.push_back(q);
     }
     if (scoef.empty()) scoef.assign(8, 0.f);
+    if (scoefn.empty()) scoefn.assign(8, 0.f);
     BigVec<double> px(c->n_pts), py(c->n_pts), pz(c->n_pts);
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < c->n_pts; p++) {
@@ -700,6 +727,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
            i_rad = add(drad.data(), drad.size() * sizeof(DevRadial)),
            i_coef = add(coef.data(), coef.size() * 8), i_coefdd = add(coef_dd.data(), coef_dd.size() * 4),
            i_scoef = add(scoef.data(), scoef.size() * 4),
+           i_coefddn = add(coef_ddn.data(), coef_ddn.size() * 4), i_scoefn = add(scoefn.data(), scoefn.size() * 4),
            i_ptsdd = add(pts_dd.data(), pts_dd.size() * 4), i_atdd = add(atom_dd.data(), atom_dd.size() * 4),
            i_snat = add(sys_nat.data(), sys_nat.size() * 4),
            i_spo = add(c->sys_pair_off.data(), c->sys_pair_off.size() * 8),
@@ -740,6 +768,8 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     P.coef = (const double *)at(i_coef);
     P.coef_dd = (const float4 *)at(i_coefdd);
     P.scoef = (const float4 *)at(i_scoef);
+    P.coef_ddn = (const float4 *)at(i_coefddn);
+    P.scoefn = (const float4 *)at(i_scoefn);
     P.pts_dd = (const float *)at(i_ptsdd);
     P.atom_dd = (const float *)at(i_atdd);
     P.sys_nat = (const int *)at(i_snat);

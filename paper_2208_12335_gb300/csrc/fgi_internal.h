@@ -47,7 +47,7 @@ struct DevShell {
     float rcut_f;         // cutoff rounded to FP32
     float inv_h_hi, inv_h_lo;   // 1/h as a double-float
     int bound_off;        // first entry of its suffix bounds of |u(r)/r| in DevPlan::rbound
-    int pad;
+    int fn0;              // first function of the shell within its species
 };
 
 struct DevBatch {
@@ -88,6 +88,12 @@ struct DevPlan {
     const double *coef;           // [sum intervals][4] FP64
     const float4 *coef_dd;        // [sum intervals][2]: the four coefficients as double-floats (hi, lo)
     const float4 *scoef;          // species on one knot grid: [interval][shell][2], the same double-floats
+    // the same two tables with every coefficient times the first
+    // normalisation constant of the radial's l (C_0 = 1/(2 sqrt pi), C_1, the
+    // xy constant of l = 2, the y(3x^2 - y^2) constant of l = 3), rounded
+    // from FP64: the lane-per-point basis kernels
+    const float4 *coef_ddn;
+    const float4 *scoefn;
     const float *pts_dd;          // [n_pts][6]: x, y, z as double-floats (xh, xl, yh, yl, zh, zl)
     const float *atom_dd;         // [n_atoms][6]: the same for atom positions
     // systems

@@ -412,23 +412,62 @@ __device__ __forceinline__ void store_zero(uint8_t *dst, long long plane, int ns
     }
 }
 
+// Ratios of the other normalisation constants of an l shell to its first
+// (the spline tables of the lane kernels hold u times the first constant):
+// l = 2: C(2z^2-x^2-y^2)/C(xy) = 1/(2 sqrt 3); l = 3: C(z(x^2-y^2))/C(y(3x^2-y^2))
+// = sqrt 6 (C(xyz) is twice that), sqrt(3/5) and sqrt(2/5).
+#define FGI_DF_CONST(c) {(float)(c), (float)((c) - (double)(float)(c))}
+__constant__ float2 kYlmRatio[4] = {
+    FGI_DF_CONST(0.28867513459481287),   // 1/(2 sqrt 3)
+    FGI_DF_CONST(2.449489742783178),     // sqrt 6
+    FGI_DF_CONST(0.7745966692414834),    // sqrt(3/5)
+    FGI_DF_CONST(0.6324555320336759)};   // sqrt(2/5)
+#undef FGI_DF_CONST
+
+// r^l Y_lm / C_l (C_l the first constant of the shell) = K_g * Q_m: Q in
+// FP32 with the exact factors 2 and 1/2 folded in, g the index of the
+// ratio K (0: K = 1).
+template <int L>
+__device__ __forceinline__ void ylm_poly_unit(float x, float y, float z, float *Q, int *g)
+{
+    if (L == 0) {
+        Q[0] = 1.f; g[0] = 0;
+    } else if (L == 1) {
+        Q[0] = y; Q[1] = z; Q[2] = x;
+        g[0] = g[1] = g[2] = 0;
+    } else if (L == 2) {
+        Q[0] = x * y; Q[1] = y * z; Q[2] = 2.f * z * z - x * x - y * y; Q[3] = x * z;
+        Q[4] = 0.5f * (x * x - y * y);
+        g[0] = 0; g[1] = 0; g[2] = 1; g[3] = 0; g[4] = 0;
+    } else {
+        const float q = 4.f * z * z - x * x - y * y;
+        Q[0] = y * (3.f * x * x - y * y); Q[1] = 2.f * (x * y * z); Q[2] = y * q;
+        Q[3] = z * (2.f * z * z - 3.f * x * x - 3.f * y * y); Q[4] = x * q; Q[5] = z * (x * x - y * y);
+        Q[6] = x * (x * x - 3.f * y * y);
+        g[0] = 0; g[1] = 1; g[2] = 2; g[3] = 3; g[4] = 2; g[5] = 1; g[6] = 0;
+    }
+}
+
 // the 2l+1 values of one shell for NIMG radial factors rk[k]
-// (= u/d^(l+1) times the image's per-point scale)
+// (= C_l u/d^(l+1) times the image's per-point scale)
 template <int L, int NIMG, class Emit>
 __device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, float z, int f0, int f_lo, int f_hi,
                                                 Emit &emit)
 {
     constexpr int NM = 2 * L + 1;
     float Q[7];
-    int ci[7];
-    ylm_poly_f32(L, x, y, z, Q, ci);
-    constexpr int NC = L < 2 ? 1 : (L == 2 ? 3 : 5);
-    constexpr int C0 = L == 0 ? 0 : (L == 1 ? 1 : (L == 2 ? 2 : 5));
-    df rc[NIMG][NC];
+    int gi[7];
+    ylm_poly_unit<L>(x, y, z, Q, gi);
+    constexpr int NG = L < 2 ? 1 : (L == 2 ? 2 : 4);
+    constexpr int G0 = L == 2 ? 0 : 1;               // first kYlmRatio entry of groups 1..
+    df rc[NIMG][NG];
 #pragma unroll
-    for (int k = 0; k < NIMG; k++)
+    for (int k = 0; k < NIMG; k++) {
+        rc[k][0] = rk[k];
 #pragma unroll
-        for (int c = 0; c < NC; c++) rc[k][c] = df_mul(rk[k], df{kYlmC[C0 + c].x, kYlmC[C0 + c].y});
+        for (int c = 1; c < NG; c++)
+            rc[k][c] = df_mul(rk[k], df{kYlmRatio[G0 + c - 1].x, kYlmRatio[G0 + c - 1].y});
+    }
     const bool whole = f0 >= f_lo && f0 + NM <= f_hi;
 #pragma unroll
     for (int m = 0; m < NM; m++) {
@@ -436,7 +475,7 @@ __device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, 
         if (!whole && (fm < f_lo || fm >= f_hi)) continue;
         df val[NIMG];
 #pragma unroll
-        for (int k = 0; k < NIMG; k++) val[k] = df_mul_f(rc[k][ci[m] - C0], Q[m]);
+        for (int k = 0; k < NIMG; k++) val[k] = df_mul_f(rc[k][gi[m]], Q[m]);
         emit(fm, val);
     }
 }
@@ -445,13 +484,16 @@ __device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, 
 // indexed from S.shell0) at the point whose double-float coordinates pp
 // holds (nullptr: no point).  emit(f, val[NIMG]) receives phi times the
 // image's scale (SCALED false: image 0 unscaled); emit0(f) a value that is
-// zero in every image (beyond the species' cutoff, or no point).  The
-// per-point scales are folded into the powers 1/d^(l+1) once per
-// (point, atom).
-template <int NIMG, bool SCALED, class Emit, class Emit0>
+// zero in every image (beyond the species' cutoff, or no point); zero_all()
+// is called by all 32 lanes of the warp, instead of emit0, when every lane
+// is beyond the cutoff or has no point (the warp's part of the image is then
+// cleared with 16-byte stores).  The per-point scales are folded into the
+// powers 1/d^(l+1) once per (point, atom).  All 32 lanes of the warp call
+// this together, for the same atom.
+template <int NIMG, bool SCALED, class Emit, class Emit0, class Zero>
 __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecies &S, const DevShell *sh_tab,
                                                int atom, const float *pp, int f_lo, int f_hi, const df *scale,
-                                               Emit &emit, Emit0 &emit0)
+                                               Emit &emit, Emit0 &emit0, Zero &zero_all)
 {
     const df zero{0.f, 0.f};
     bool none = pp == nullptr;
@@ -465,19 +507,29 @@ __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecie
         const float rcs = (float)S.rcut * 1.00001f;
         none = xf * xf + yf * yf + zf * zf > rcs * rcs;
     }
+    if (__all_sync(0xffffffffu, none)) {
+        zero_all();
+        return;
+    }
     if (none) {
         for (int f = f_lo; f < f_hi; f++) emit0(f);
         return;
     }
-    const df x = df_sub(df{pp[0], pp[1]}, df{aa[0], aa[1]});
-    const df y = df_sub(df{pp[2], pp[3]}, df{aa[2], aa[3]});
-    const df z = df_sub(df{pp[4], pp[5]}, df{aa[4], aa[5]});
-    const df d = df_sqrt(df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z)));
-    const bool origin = d.hi < 1e-12f;
+    // offset from the atom (the rounding of the low parts differs from point
+    // to point), d^2 (terms of one sign), 1/d from a refined rsqrtf, d = d^2/d
+    const df x = df_sub_sloppy(df{pp[0], pp[1]}, df{aa[0], aa[1]});
+    const df y = df_sub_sloppy(df{pp[2], pp[3]}, df{aa[2], aa[3]});
+    const df z = df_sub_sloppy(df{pp[4], pp[5]}, df{aa[4], aa[5]});
+    const df d2 = df_add_sloppy(df_add_sloppy(df_mul(x, x), df_mul(y, y)), df_mul(z, z));
+    const bool origin = d2.hi < 1e-24f;                 // d < 1e-12
+    df d = zero, i0 = zero;
+    if (!origin) {
+        i0 = df_rsqrt(d2);
+        d = df_mul(d2, i0);
+    }
     // 1/d^(l+1) for l <= lmax, times each image's scale
     df ip[NIMG][4];
     {
-        df i0 = origin ? zero : df_rcp(d);
         df pw[4];
         pw[0] = i0;
         pw[1] = S.lmax >= 1 ? df_mul(i0, i0) : zero;
@@ -499,7 +551,7 @@ __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecie
         kk = max(0, min(kk, S.nk - 2));
         t = sd.hi - (float)kk;
         tl = sd.lo;
-        sc = P.scoef + S.scoef_off + 2 * ((long long)kk * S.n_shell);
+        sc = P.scoefn + S.scoef_off + 2 * ((long long)kk * S.n_shell);
     }
     int f = 0;
     for (int sh = 0; sh < S.n_shell; sh++) {
@@ -509,14 +561,14 @@ __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecie
             f += nm;
             continue;
         }
-        df uu = zero;                                   // u(d), or its limit u'(0) d at the origin
+        df uu = zero;                                   // C_l u(d), or its limit C_0 u'(0) d at the origin
         bool live = d.hi < R.rcut_f;
         if (live) {
             if (origin) {
                 live = R.l == 0;
                 if (live) {
-                    const float4 ch = __ldg(P.coef_dd + 2 * R.coef_off), cl = __ldg(P.coef_dd + 2 * R.coef_off + 1);
-                    uu = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});   // the l = 0 limit c1/h
+                    const float4 ch = __ldg(P.coef_ddn + 2 * R.coef_off), cl = __ldg(P.coef_ddn + 2 * R.coef_off + 1);
+                    uu = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});   // the l = 0 limit C_0 c1/h
                 }
             } else {
                 const float4 *ce;
@@ -533,7 +585,7 @@ __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecie
                         t = s2.hi - (float)kk;
                         tl = s2.lo;
                     }
-                    ce = P.coef_dd + 2 * (R.coef_off + kk);
+                    ce = P.coef_ddn + 2 * (R.coef_off + kk);
                 }
                 // u = c0 + t c1 + t^2 (c2 + t c3): c0 + t c1 in double-float
                 const float4 ch = __ldg(ce);
@@ -619,10 +671,24 @@ __device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &
 #pragma unroll
             for (int k = 0; k < NIMG; k++) store_zero((k == 0 ? img0 : img1) + off, T.plane_phi, NSPLIT);
         };
+        // the warp's 32 columns of rows rb + [f_lo, f_hi): four 16-byte units
+        // per row and plane
+        auto zero_all = [&]() {
+            const int pc = q * 32;
+            for (int u = lane; u < (f_hi - f_lo) * 4; u += 32) {
+                const int off = elem_offset(I, T.nc_alloc, rb + f_lo + (u >> 2), pc + (u & 3) * 8);
+#pragma unroll
+                for (int k = 0; k < NIMG; k++)
+#pragma unroll
+                    for (int pl = 0; pl < NSPLIT; pl++)
+                        *reinterpret_cast<uint4 *>((k == 0 ? img0 : img1) + off + pl * T.plane_phi) =
+                            make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
         if (NIMG == 1)
-            eval_atom_lane<1, true>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0);
+            eval_atom_lane<1, true>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0, zero_all);
         else
-            eval_atom_lane<2, false>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0);
+            eval_atom_lane<2, false>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0, zero_all);
     }
 }
 
@@ -640,6 +706,19 @@ __device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &
 // rounding varies from point to point).
 
 constexpr int kPhiThreads = 256;
+constexpr int kDistCacheFloats = 128 * kPhiValStride * 2;     // the dynamic buffer, as floats
+
+// FP32 distance from atom `atom` to point `pt` (from the double-float
+// coordinates), for the bounds of the digit grids
+__device__ __forceinline__ float point_atom_dist_f32(const DevPlan &P, int atom, long long pt)
+{
+    const float *aa = P.atom_dd + 6 * atom;
+    const float *pp = P.pts_dd + 6 * pt;
+    const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
+    const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
+    const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
+    return sqrtf(x * x + y * y + z * z);
+}
 
 __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBatch *tb, const WorkItem *items,
                                                 uint8_t *ws, const double *v, int n_split, int fixed,
@@ -694,45 +773,50 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
             const float a = fabsf((float)(P.pw[B.pt0 + p] * v[B.pt0 + p])) * (1.f + 1.f / 1048576.f);
             wvf[p] = fminf(sgn != 0 ? sqrtf(a) * (1.f + 1.f / 1048576.f) : a, 1.0e30f);
         }
+        // distances of the block's atoms to the batch's points (FP32), once,
+        // in the dynamic buffer when they fit
+        float *dcache = reinterpret_cast<float *>(phi_smem);
+        const bool dcached = ne * B.np <= kDistCacheFloats;
+        if (dcached) {
+            for (int q = threadIdx.x; q < ne * B.np; q += blockDim.x) {
+                const int eq = q / B.np, p = q - eq * B.np;
+                dcache[q] = point_atom_dist_f32(P, act[e0 + eq].atom, B.pt0 + p);
+            }
+        }
         __syncthreads();
-        // warp tasks (atom of the block, 32-point group), lane = point: the
-        // point's distance once, then per shell one lookup; the warp reduces
-        // each shell's maxima and sums over its 32 points and lane 0 folds
-        // them into the rows (shared-memory atomics across the groups)
+        // warp tasks (atom of the block, shell): the lanes stride over the
+        // batch's points, one lookup per point, and keep the maxima and sums in
+        // registers; one warp reduction per task, whose rows it alone writes
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-        const int ng = (B.np + 31) >> 5;
-        for (int task = warp; task < ne * ng; task += nwarp) {
-            const int eq = task / ng, q = task - eq * ng;
-            const DevAct A = act[e0 + eq];
+        int job0 = 0;
+        for (int e = e0; e <= e1; e++) {
+            const DevAct A = act[e];
             const DevSpecies S = P.species[P.atom_species[A.atom]];
             const int f_lo = max(0, r0 - A.fn_loc), f_hi = min(S.n_fn, r0 + 128 - A.fn_loc);
-            const int p = q * 32 + lane;
-            float d = 3.0e38f, wp = 0.f;
-            if (p < B.np) {
-                const float *aa = P.atom_dd + 6 * A.atom;
-                const float *pp = P.pts_dd + 6 * (B.pt0 + p);
-                const float x = (pp[0] - aa[0]) + (pp[1] - aa[1]);
-                const float y = (pp[2] - aa[2]) + (pp[3] - aa[3]);
-                const float z = (pp[4] - aa[4]) + (pp[5] - aa[5]);
-                d = sqrtf(x * x + y * y + z * z);
-                wp = wvf[p];
-            }
-            int f = 0;
-            for (int sh = 0; sh < S.n_shell; sh++) {
+            const int first = ((warp - job0) % nwarp + nwarp) % nwarp;
+            job0 += S.n_shell;
+            for (int sh = first; sh < S.n_shell; sh += nwarp) {
                 const DevShell R = sh_tab[S.shell0 + sh];
-                const int nm = 2 * R.l + 1;
-                const int f1 = f;
-                f += nm;
-                if (f <= f_lo || f1 >= f_hi) continue;
-                float t = 0.f;
-                if (d < R.rcut_f * 1.00001f) {
-                    const int ki = min(max((int)(d * 0.999999f * R.inv_h_hi), 0), R.nk - 2);
-                    t = __ldg(P.rbound + R.bound_off + ki);
+                const int nm = 2 * R.l + 1, f1 = R.fn0;
+                if (f1 + nm <= f_lo || f1 >= f_hi) continue;
+                const float rcl = R.rcut_f * 1.00001f;
+                const float *bt = P.rbound + R.bound_off;
+                float m0 = 0.f, m1 = 0.f, s0 = 0.f, s1 = 0.f;
+                for (int p = lane; p < B.np; p += 32) {
+                    const float d = dcached ? dcache[(e - e0) * B.np + p] : point_atom_dist_f32(P, A.atom, B.pt0 + p);
+                    if (d < rcl) {
+                        // knot index taken from below against FP32 rounding of d
+                        const int ki = min(max((int)(d * 0.999999f * R.inv_h_hi), 0), R.nk - 2);
+                        const float t = __ldg(bt + ki);
+                        const float tw = t * wvf[p];
+                        m0 = fmaxf(m0, t);
+                        m1 = fmaxf(m1, tw);
+                        s0 += t;
+                        s1 += tw;
+                    }
                 }
-                const float tw = t * wp;
-                const float m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(t)));
-                const float m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(tw)));
-                float s0 = t, s1 = tw;
+                m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
+                m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -743,10 +827,10 @@ __global__ void __launch_bounds__(kPhiThreads, 4) k_tc_phi(DevPlan P, const TcBa
                 if (lane < nm && m0 > 0.f && fr >= f_lo && fr < f_hi) {
                     const int row = A.fn_loc + fr - r0;
                     const float yl = __ldg(P.rbound + R.l * R.l + lane);
-                    atomicMax(&rowmax[0][row], __float_as_uint(fminf(m0 * yl, 1.0e30f)));
-                    atomicMax(&rowmax[1][row], __float_as_uint(fminf(m1 * yl, 1.0e30f)));
-                    atomicAdd(&rowsum[0][row], fminf(s0 * 1.0001f * yl, 1.0e30f));   // 1.0001: FP32 sums
-                    atomicAdd(&rowsum[1][row], fminf(s1 * 1.0001f * yl, 1.0e30f));
+                    rowmax[0][row] = __float_as_uint(fminf(m0 * yl, 1.0e30f));
+                    rowmax[1][row] = __float_as_uint(fminf(m1 * yl, 1.0e30f));
+                    rowsum[0][row] = fminf(s0 * 1.0001f * yl, 1.0e30f);   // 1.0001: FP32 sums
+                    rowsum[1][row] = fminf(s1 * 1.0001f * yl, 1.0e30f);
                 }
             }
         }
@@ -1023,7 +1107,17 @@ __global__ void __launch_bounds__(kPhiThreads, 5) k_tc_phi_cols(DevPlan P, const
             const int rg = A.fn_loc + f;
             store_zero(phi_img + elem_offset(rg >> 7, T.nc_alloc, rg & 127, p), T.plane_phi, nsplit);
         };
-        eval_atom_lane<1, false>(P, S, sh_tab, A.atom, pp, 0, S.n_fn, nullptr, emit, emit0);
+        // the warp's 32 columns of the atom's rows: four 16-byte units per row and plane
+        auto zero_all = [&]() {
+            const int pc = c * 64 + (task & 1) * 32;
+            for (int u = lane; u < S.n_fn * 4; u += 32) {
+                const int rg = A.fn_loc + (u >> 2);
+                const int off = elem_offset(rg >> 7, T.nc_alloc, rg & 127, pc + (u & 3) * 8);
+                for (int pl = 0; pl < nsplit; pl++)
+                    *reinterpret_cast<uint4 *>(phi_img + off + pl * T.plane_phi) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        eval_atom_lane<1, false>(P, S, sh_tab, A.atom, pp, 0, S.n_fn, nullptr, emit, emit0, zero_all);
     }
     // rows [n_b, 64 nkc) of the contraction's last function chunk: zeros
     const int nplanes = fixed ? 3 : 1;
@@ -2166,8 +2260,8 @@ cudaError_t tc_launch_phi(const TcPlan &t, const DevPlan &P, const TcWave &w, co
     // the H images (v given) of the split mode use the fixed-point leading term
     const int fixed = (v != nullptr && n_split == 3) ? 1 : 0;
     // the dynamic buffer caches geometry for the FP32 pass over the points
-    // (bound_grids 0 and 1); the table-bound H pass needs none
-    const size_t dyn = t.bound_grids >= 2 ? 0 : smem_phi();
+    // (bound_grids 0 and 1), or the point-atom distances of the table-bound pass
+    const size_t dyn = smem_phi();
     k_tc_phi<<<(unsigned)w.nphi, kPhiThreads, dyn, s>>>(P, t.d_batches, t.d_items + w.phi0,
                                                        (uint8_t *)ws + t.img_base, v, n_split, fixed,
                                                        reinterpret_cast<int *>((uint8_t *)ws + t.sign_off),
