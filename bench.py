@@ -738,6 +738,12 @@ def main():
                 r["frac"] = r["achieved"] / r["peak"]
                 # the committed DRAM figures were taken on the split-BF16 kernels
                 r["traffic"] = traffic_for(kind) if args.precision == "split_bf16" else None
+                # the DRAM traffic against the algorithmic bytes of the class
+                # (operand images written and read, scatter, D blocks, points)
+                alg_bytes = pk["bytes"] / max(1, pk["launches"])
+                r["algorithmic_bytes"] = alg_bytes
+                r["traffic_over_algorithmic"] = (r["traffic"] / alg_bytes
+                                                 if r["traffic"] is not None and alg_bytes > 0 else None)
                 r["launch_ms"] = avg_ms
                 r["launches_per_step"] = pk["launches"] / args.steps
                 return r
@@ -745,7 +751,8 @@ def main():
             dom = max(("basis", "h", "density"), key=lambda k: prof[k]["ms"])
             roof = roofline(dom)
             # the other kernel classes, for context (the line above is the dominant one)
-            roof_all = {k: {q: roofline(k)[q] for q in ("bound", "achieved", "peak", "unit", "frac")}
+            roof_all = {k: {q: roofline(k)[q] for q in ("bound", "achieved", "peak", "unit", "frac", "traffic",
+                                                         "algorithmic_bytes", "traffic_over_algorithmic")}
                         for k in ("basis", "h", "density")}
         cpu = None
         errors = None

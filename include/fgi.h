@@ -194,7 +194,14 @@ int fgi_workspace_size(fgi_ctx *ctx, size_t *bytes);
 /* H integration: h[val] (+)= sum_b sum_{p in b} w_p v_p phi_i phi_j for every
    stored (i, j).  v_dev: device [n_pts] FP64; h_dev: device [nnz] FP64,
    overwritten (accumulate = 0) or added to (accumulate = 1).  Cross-batch
-   accumulation is FP64 in every precision. */
+   accumulation: FP64 on the FP64 path; on the split-BF16 and BF16 paths an
+   exact 64-bit fixed-point sum with unit 2^-40 Ha (bitwise reproducible,
+   the FP32 tile results rounded to the unit), converted to FP64 once at the
+   end.  Limits of that sum: one super-batch's contribution to an entry
+   must stay below 2^22 Ha (beyond it the status word reports
+   FGI_ERR_NONFINITE at the next fgi_sync), and every entry's running sum
+   below 2^23 Ha (beyond it the 64-bit sum would wrap; this is not checked,
+   and no Hamiltonian of the method comes near it). */
 int fgi_integrate_h(fgi_ctx *ctx, const double *v_dev, double *h_dev, int accumulate,
                     void *ws, size_t ws_bytes, void *stream);
 

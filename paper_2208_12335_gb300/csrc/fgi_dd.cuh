@@ -73,6 +73,15 @@ __device__ __forceinline__ df df_mul_f(df a, float b)
     return df_fast_two_sum(p.hi, p.lo);
 }
 
+// The same product without the final renormalisation: hi = fl(a.hi b) and
+// lo the rest, |lo| up to about two ulps of hi.  For consumers that use the
+// pair only as the sum hi + lo (the split into BF16 terms).
+__device__ __forceinline__ df df_mul_f_raw(df a, float b)
+{
+    const float p = a.hi * b;
+    return {p, fmaf(a.lo, b, fmaf(a.hi, b, -p))};
+}
+
 // sqrt by one Newton correction of the FP32 root (IEEE sqrtf)
 __device__ __forceinline__ df df_sqrt(df a)
 {

@@ -625,7 +625,7 @@ int build_plan(fgi_ctx *c, const char *tune_path)
     // interleaved by interval, so that one point's shells read neighbouring
     // cache lines
     std::vector<float> scoef, scoefn;
-    std::vector<int> shell_fn0;
+    std::vector<int> shell_fn0, shell_by_l;     // per species slot: first function, radial (grouped by l)
     for (const SpeciesH &s : c->species) {
         DevSpecies d{};
         d.shell0 = (int)shell_rad.size();
@@ -637,6 +637,21 @@ int build_plan(fgi_ctx *c, const char *tune_path)
             shared = shared && c->radials[sh].h == c->radials[s.shells[0]].h &&
                      c->radials[sh].nk == c->radials[s.shells[0]].nk;
         d.shared_grid = shared ? 1 : 0;
+        // the shells grouped by l (stable), with each one's first function
+        std::vector<int> first(s.shells.size()), lord;
+        {
+            int fn = 0;
+            for (size_t i = 0; i < s.shells.size(); i++) {
+                first[i] = fn;
+                fn += 2 * c->radials[s.shells[i]].l + 1;
+            }
+            for (int l = 0; l <= 3; l++)
+                for (size_t i = 0; i < s.shells.size(); i++)
+                    if (c->radials[s.shells[i]].l == l) {
+                        lord.push_back((int)i);
+                        d.nl[l]++;
+                    }
+        }
         if (shared) {
             const RadialH &r0 = c->radials[s.shells[0]];
             d.nk = r0.nk;
@@ -647,22 +662,25 @@ int build_plan(fgi_ctx *c, const char *tune_path)
                 for (int sh : s.shells) {
                     const size_t src = 8 * ((size_t)drad[sh].coef_off + k);
                     scoef.insert(scoef.end(), coef_dd.begin() + src, coef_dd.begin() + src + 8);
+                }
+            for (int k = 0; k < r0.nk - 1; k++)
+                for (int i : lord) {
+                    const size_t src = 8 * ((size_t)drad[s.shells[i]].coef_off + k);
                     scoefn.insert(scoefn.end(), coef_ddn.begin() + src, coef_ddn.begin() + src + 8);
                 }
         }
         shell_rad.insert(shell_rad.end(), s.shells.begin(), s.shells.end());
-        int fn = 0;
-        for (int sh : s.shells) {
-            shell_fn0.push_back(fn);
-            fn += 2 * c->radials[sh].l + 1;
+        for (int i : lord) {
+            shell_fn0.push_back(first[i]);
+            shell_by_l.push_back(s.shells[i]);
         }
         d.lmax = 0;
         for (int sh : s.shells) d.lmax = std::max(d.lmax, c->radials[sh].l);
         dsp.push_back(d);
     }
     std::vector<DevShell> dshell;
-    for (size_t i = 0; i < shell_rad.size(); i++) {
-        const DevRadial &R = drad[shell_rad[i]];
+    for (size_t i = 0; i < shell_by_l.size(); i++) {
+        const DevRadial &R = drad[shell_by_l[i]];
         DevShell q{};
         q.coef_off = (int)R.coef_off;
         q.nk = R.nk;

@@ -36,10 +36,14 @@ struct DevSpecies {
     int nk;               // shared grid: knots
     float inv_h_hi, inv_h_lo;   // shared grid: 1/h as a double-float
     int lmax;             // largest angular momentum of its shells
+    int nl[4];            // shells of each l (DevPlan::shells holds them grouped by l)
 };
 
 // One radial shell of a species (index shell0 + sh), the fields the
-// tensor-core basis kernels read, packed in 32 bytes.
+// tensor-core basis kernels read, packed in 32 bytes.  Within a species the
+// entries are grouped by l (ascending, otherwise in input order); fn0 gives
+// each shell's place among the species' functions, so that the order of
+// evaluation does not change which row a value lands in.
 struct DevShell {
     int coef_off;         // first interval of the radial in coef_dd (units of 4 coefficients)
     int nk;               // knots
@@ -91,7 +95,8 @@ struct DevPlan {
     // the same two tables with every coefficient times the first
     // normalisation constant of the radial's l (C_0 = 1/(2 sqrt pi), C_1, the
     // xy constant of l = 2, the y(3x^2 - y^2) constant of l = 3), rounded
-    // from FP64: the lane-per-point basis kernels
+    // from FP64: the lane-per-point basis kernels.  scoefn interleaves the
+    // shells in the order of DevPlan::shells (grouped by l).
     const float4 *coef_ddn;
     const float4 *scoefn;
     const float *pts_dd;          // [n_pts][6]: x, y, z as double-floats (xh, xl, yh, yl, zh, zl)

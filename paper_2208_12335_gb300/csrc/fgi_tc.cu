@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fgi.h"
@@ -372,28 +373,9 @@ __device__ __forceinline__ const float4 *spline_tab(const DevPlan &P, const DevS
 // image row per plane.  The geometry (offset, distance, 1/d^(l+1)) is
 // double-float once per (point, atom); the radial factor once per shell,
 // times the per-point scale of each image; the angular polynomial FP32.
-
-// 16-bit store of the BF16 bits of each plane
-__device__ __forceinline__ void store_bf16x3(uint8_t *dst, long long plane, __nv_bfloat16 a, __nv_bfloat16 b,
-                                             __nv_bfloat16 c)
-{
-    *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(a);
-    *reinterpret_cast<unsigned short *>(dst + plane) = __bfloat16_as_ushort(b);
-    *reinterpret_cast<unsigned short *>(dst + 2 * plane) = __bfloat16_as_ushort(c);
-}
-
-// NSPLIT 3: the fixed-point split on the grid (scale, unit); 1: plain BF16
-template <int NSPLIT>
-__device__ __forceinline__ void store_value(uint8_t *dst, long long plane, df x, float scale, float unit)
-{
-    if (NSPLIT == 3) {
-        __nv_bfloat16 a, b, c;
-        split_fixed(x, scale, unit, a, b, c);
-        store_bf16x3(dst, plane, a, b, c);
-    } else {
-        *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(__float2bfloat16_rn(x.hi));
-    }
-}
+// (Two points per lane with 32-bit stores of BF16 pairs was measured
+// slower: the doubled per-lane state costs occupancy or spills, and these
+// kernels wait mostly on their loads.)
 
 // byte offset of element (row r, point p) in the image chunk grid of block I
 // (below 2^31: a batch's image plane is at most 64 blocks x 16 chunks x 16 KB)
@@ -401,6 +383,22 @@ __device__ __forceinline__ int elem_offset(int I, int nc_alloc, int r, int p)
 {
     const int g = (p >> 3) & 7;
     return ((I * nc_alloc + (p >> 6)) * 16 + (r >> 3)) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4) + (p & 7) * 2;
+}
+
+// One value split on its row's or point's grid (split_fixed; NSPLIT 1:
+// plain BF16) and stored as one 16-bit BF16 per plane
+template <int NSPLIT>
+__device__ __forceinline__ void store_value(uint8_t *dst, long long plane, df x, float scale, float unit)
+{
+    if (NSPLIT == 3) {
+        __nv_bfloat16 a, b, c;
+        split_fixed(x, scale, unit, a, b, c);
+        *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(a);
+        *reinterpret_cast<unsigned short *>(dst + plane) = __bfloat16_as_ushort(b);
+        *reinterpret_cast<unsigned short *>(dst + 2 * plane) = __bfloat16_as_ushort(c);
+    } else {
+        *reinterpret_cast<unsigned short *>(dst) = __bfloat16_as_ushort(__float2bfloat16_rn(x.hi));
+    }
 }
 
 __device__ __forceinline__ void store_zero(uint8_t *dst, long long plane, int nsplit)
@@ -448,18 +446,19 @@ __device__ __forceinline__ void ylm_poly_unit(float x, float y, float z, float *
     }
 }
 
-// the 2l+1 values of one shell for NIMG radial factors rk[k]
-// (= C_l u/d^(l+1) times the image's per-point scale)
+// the 2l+1 values of one shell for NIMG radial factors rk[k] (= C_l
+// u/d^(l+1) times the image's per-point scale), handed to the emitter as
+// unnormalised double-floats (the split uses hi + lo only)
 template <int L, int NIMG, class Emit>
 __device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, float z, int f0, int f_lo, int f_hi,
                                                 Emit &emit)
 {
     constexpr int NM = 2 * L + 1;
-    float Q[7];
-    int gi[7];
-    ylm_poly_unit<L>(x, y, z, Q, gi);
     constexpr int NG = L < 2 ? 1 : (L == 2 ? 2 : 4);
     constexpr int G0 = L == 2 ? 0 : 1;               // first kYlmRatio entry of groups 1..
+    float Q[NM];
+    int gi[7];
+    ylm_poly_unit<L>(x, y, z, Q, gi);
     df rc[NIMG][NG];
 #pragma unroll
     for (int k = 0; k < NIMG; k++) {
@@ -475,7 +474,7 @@ __device__ __forceinline__ void emit_shell_lane(const df *rk, float x, float y, 
         if (!whole && (fm < f_lo || fm >= f_hi)) continue;
         df val[NIMG];
 #pragma unroll
-        for (int k = 0; k < NIMG; k++) val[k] = df_mul_f(rc[k][gi[m]], Q[m]);
+        for (int k = 0; k < NIMG; k++) val[k] = df_mul_f_raw(rc[k][gi[m]], Q[m]);
         emit(fm, val);
     }
 }
@@ -553,73 +552,69 @@ __device__ __forceinline__ void eval_atom_lane(const DevPlan &P, const DevSpecie
         tl = sd.lo;
         sc = P.scoefn + S.scoef_off + 2 * ((long long)kk * S.n_shell);
     }
-    int f = 0;
-    for (int sh = 0; sh < S.n_shell; sh++) {
-        const DevShell R = sh_tab[S.shell0 + sh];
-        const int nm = 2 * R.l + 1;
-        if (f + nm <= f_lo || f >= f_hi) {
-            f += nm;
-            continue;
-        }
-        df uu = zero;                                   // C_l u(d), or its limit C_0 u'(0) d at the origin
-        bool live = d.hi < R.rcut_f;
-        if (live) {
-            if (origin) {
-                live = R.l == 0;
-                if (live) {
-                    const float4 ch = __ldg(P.coef_ddn + 2 * R.coef_off), cl = __ldg(P.coef_ddn + 2 * R.coef_off + 1);
-                    uu = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});   // the l = 0 limit C_0 c1/h
-                }
-            } else {
-                const float4 *ce;
-                if (sc) {
-                    ce = sc + 2 * sh;
-                } else {
-                    if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
-                        grid_hi = R.inv_h_hi;
-                        grid_lo = R.inv_h_lo;
-                        grid_nk = R.nk;
-                        const df s2 = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
-                        kk = (int)floorf(s2.hi);
-                        kk = max(0, min(kk, R.nk - 2));
-                        t = s2.hi - (float)kk;
-                        tl = s2.lo;
+    // the shells grouped by l: the power 1/d^(l+1) and the angular
+    // polynomial's form are fixed within a group
+    int sh = 0;
+    auto shells_of_l = [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        constexpr int NM = 2 * L + 1;
+        const int end = sh + S.nl[L];
+        for (; sh < end; sh++) {
+            const DevShell R = sh_tab[S.shell0 + sh];
+            const int f = R.fn0;
+            if (f + NM <= f_lo || f >= f_hi) continue;
+            df uu = zero;                               // C_l u(d), or its limit C_0 u'(0) d at the origin
+            bool live = d.hi < R.rcut_f;
+            if (live) {
+                if (origin) {
+                    live = L == 0;
+                    if (live) {
+                        const float4 ch = __ldg(P.coef_ddn + 2 * R.coef_off), cl = __ldg(P.coef_ddn + 2 * R.coef_off + 1);
+                        uu = df_mul(df{ch.y, cl.y}, df{R.inv_h_hi, R.inv_h_lo});   // the l = 0 limit C_0 c1/h
                     }
-                    ce = P.coef_ddn + 2 * (R.coef_off + kk);
+                } else {
+                    const float4 *ce;
+                    if (sc) {
+                        ce = sc + 2 * sh;
+                    } else {
+                        if (R.inv_h_hi != grid_hi || R.inv_h_lo != grid_lo || R.nk != grid_nk) {
+                            grid_hi = R.inv_h_hi;
+                            grid_lo = R.inv_h_lo;
+                            grid_nk = R.nk;
+                            const df s2 = df_mul(d, df{R.inv_h_hi, R.inv_h_lo});
+                            kk = (int)floorf(s2.hi);
+                            kk = max(0, min(kk, R.nk - 2));
+                            t = s2.hi - (float)kk;
+                            tl = s2.lo;
+                        }
+                        ce = P.coef_ddn + 2 * (R.coef_off + kk);
+                    }
+                    // u = c0 + t c1 + t^2 (c2 + t c3): c0 + t c1 in double-float
+                    const float4 ch = __ldg(ce);
+                    const float4 cl = __ldg(ce + 1);
+                    const df lin = df_two_prod(t, ch.y);
+                    const float lin_lo = fmaf(t, cl.y, fmaf(tl, ch.y, lin.lo));
+                    const float quad = (t * t) * fmaf(t, ch.w, ch.z);
+                    uu = df_two_sum(ch.x, lin.hi);
+                    uu = df_two_sum(uu.hi, uu.lo + ((cl.x + lin_lo) + quad));
                 }
-                // u = c0 + t c1 + t^2 (c2 + t c3): c0 + t c1 in double-float
-                const float4 ch = __ldg(ce);
-                const float4 cl = __ldg(ce + 1);
-                const df lin = df_two_prod(t, ch.y);
-                const float lin_lo = fmaf(t, cl.y, fmaf(tl, ch.y, lin.lo));
-                const float quad = (t * t) * fmaf(t, ch.w, ch.z);
-                uu = df_two_sum(ch.x, lin.hi);
-                uu = df_two_sum(uu.hi, uu.lo + ((cl.x + lin_lo) + quad));
             }
-        }
-        if (!live) {
-            const int m0 = max(f, f_lo), m1 = min(f + nm, f_hi);
-            for (int m = m0; m < m1; m++) emit0(m);
-            f += nm;
-            continue;
-        }
-        df rk[NIMG];
-        if (origin) {
-#pragma unroll
-            for (int k = 0; k < NIMG; k++) rk[k] = (SCALED || k > 0) ? df_mul(uu, scale[k]) : uu;
-        } else {
+            if (!live) {
+                const int m0 = max(f, f_lo), m1 = min(f + NM, f_hi);
+                for (int m = m0; m < m1; m++) emit0(m);
+                continue;
+            }
+            df rk[NIMG];
 #pragma unroll
             for (int k = 0; k < NIMG; k++)
-                rk[k] = df_mul(uu, R.l == 0 ? ip[k][0] : (R.l == 1 ? ip[k][1] : (R.l == 2 ? ip[k][2] : ip[k][3])));
+                rk[k] = origin ? ((SCALED || k > 0) ? df_mul(uu, scale[k]) : uu) : df_mul(uu, ip[k][L]);
+            emit_shell_lane<L, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit);
         }
-        switch (R.l) {
-        case 0: emit_shell_lane<0, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
-        case 1: emit_shell_lane<1, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
-        case 2: emit_shell_lane<2, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
-        default: emit_shell_lane<3, NIMG>(rk, x.hi, y.hi, z.hi, f, f_lo, f_hi, emit); break;
-        }
-        f += nm;
-    }
+    };
+    shells_of_l(std::integral_constant<int, 0>{});
+    if (S.lmax >= 1) shells_of_l(std::integral_constant<int, 1>{});
+    if (S.lmax >= 2) shells_of_l(std::integral_constant<int, 2>{});
+    if (S.lmax >= 3) shells_of_l(std::integral_constant<int, 3>{});
 }
 
 // the species' shells for one CTA: shared memory when they fit
@@ -651,10 +646,10 @@ __device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &
         const int p = q * 32 + lane;
         const bool live = p < B.np;
         const float *pp = live ? P.pts_dd + 6 * (B.pt0 + p) : nullptr;
-        df scale[2];
+        df scale[NIMG];
         const float2 s2 = live ? wvs[p] : make_float2(0.f, 0.f);
-        scale[0] = df{s2.x, s2.y};
-        scale[1] = scale[0];
+#pragma unroll
+        for (int k = 0; k < NIMG; k++) scale[k] = df{s2.x, s2.y};
         const int rb = A.fn_loc - r0;
         auto emit = [&](int f, const df *val) {
             const int r = rb + f;
@@ -685,10 +680,7 @@ __device__ __forceinline__ void h_image_lanes(const DevPlan &P, const DevBatch &
                             make_uint4(0u, 0u, 0u, 0u);
             }
         };
-        if (NIMG == 1)
-            eval_atom_lane<1, true>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0, zero_all);
-        else
-            eval_atom_lane<2, false>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0, zero_all);
+        eval_atom_lane<NIMG, NIMG == 1>(P, S, sh_tab, A.atom, pp, f_lo, f_hi, scale, emit, emit0, zero_all);
     }
 }
 

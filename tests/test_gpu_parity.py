@@ -343,6 +343,42 @@ def spdf_molecule():
     return prob, B, O.h_matrix(B, prob.pts, prob.w, prob.v)
 
 
+@pytest.fixture(scope="module")
+def shuffled_shells_molecule():
+    """Two species whose shells are not in order of l: Y with s, p, d, f and
+    Z with f, s, d, s, p (17 functions), atoms Y Z Y.  The lane kernels walk
+    each species' shells grouped by l; every value must still land in the
+    row of its function."""
+    rc = 4.0 * W.BOHR_PER_ANG
+    ron = rc - 1.0 * W.BOHR_PER_ANG
+    specs = [W.RadialSpec(l, (0.5 + 0.15 * l, 1.4), (1.0, -0.25), rc, ron, 2000) for l in range(4)]
+    specs.append(W.RadialSpec(0, (0.35, 2.2), (0.8, 0.3), rc, ron, 2000))
+    radials = [W.make_radial(s) for s in specs]
+    species = [W.Species("Y", 4.0, [0, 1, 2, 3]), W.Species("Z", 5.0, [3, 0, 2, 4, 1])]
+    xyz = np.array([[0.0, 0.0, 0.0], [2.3, 0.4, -0.3], [-0.8, 2.1, 1.1]])
+    prob = W.build_problem("spdf2", radials, species, [(np.array([0, 1, 0], dtype=np.int32), xyz)],
+                           lambda sp: (24, 50), 9, (200, 50, None))
+    B = O.system_basis(prob)
+    return prob, B, O.h_matrix(B, prob.pts, prob.w, prob.v)
+
+
+@pytest.mark.parametrize("precision,tol", PRECISIONS)
+def test_h_and_density_with_shells_out_of_l_order(fgi, shuffled_shells_molecule, precision, tol):
+    prob, B, H = shuffled_shells_molecule
+    assert B.n_fn == 16 + 17 + 16
+    ctx = fgi.Context(0).load(prob, precision)
+    h = ctx.integrate_h(dev(prob.v)).cpu().numpy()
+    D, _ = W.density_matrix_occ(B.n_fn, 12, np.random.default_rng(13))
+    n, _ = ctx.density(dev(stored(ctx, D)))
+    ctx.sync()
+    err = np.max(np.abs(h - stored(ctx, H)))
+    bound = TOL_FP64 * np.abs(H).max() if tol is None else tol
+    assert err <= bound, (precision, err, np.abs(H).max())
+    nref = O.density(B, prob.pts, D)
+    rel = np.linalg.norm(n.cpu().numpy() - nref) / np.linalg.norm(nref)
+    assert rel <= {"fp64": 1e-12, "split_bf16": TOL_SPLIT_N, "bf16": 1e-2}[precision], rel
+
+
 @pytest.mark.parametrize("precision,tol", PRECISIONS)
 def test_h_and_density_with_f_functions(fgi, spdf_molecule, precision, tol):
     prob, B, H = spdf_molecule
