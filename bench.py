@@ -182,9 +182,9 @@ def fp32_alu_peak(torch, mhz):
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def traffic_for(kind):
+def traffic_for(kind, workload="chno1000"):
     """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+    on the current kernel source and for this workload; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -200,6 +200,8 @@ def traffic_for(kind):
     except Exception:
         return None
     if h != ent.get("source_sha256_16"):
+        return None
+    if ent.get("workload", "chno1000") != workload:
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -737,7 +739,7 @@ def main():
                                       % (peak_src, products)}
                 r["frac"] = r["achieved"] / r["peak"]
                 # the committed DRAM figures were taken on the split-BF16 kernels
-                r["traffic"] = traffic_for(kind) if args.precision == "split_bf16" else None
+                r["traffic"] = traffic_for(kind, args.workload) if args.precision == "split_bf16" else None
                 # the DRAM traffic against the algorithmic bytes of the class
                 # (operand images written and read, scatter, D blocks, points)
                 alg_bytes = pk["bytes"] / max(1, pk["launches"])

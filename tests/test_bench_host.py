@@ -70,6 +70,7 @@ def test_traffic_record_only_for_the_current_kernel_source(tmp_path, monkeypatch
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.traffic_for("h") == 123.0
     assert bench.traffic_for("density") is None
+    assert bench.traffic_for("h", "si64") is None              # taken on another workload
     src.write_bytes(b"kernel source v2\n")                 # the kernel changed since the capture
     assert bench.traffic_for("h") is None
 
