@@ -183,8 +183,10 @@ def fp32_alu_peak(torch, mhz):
 
 
 def traffic_for(kind, workload="chno1000"):
-    """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source and for this workload; else None."""
+    """DRAM bytes per algorithmic flop of a kernel class from the committed
+    ncu summary, if it was taken on the current kernel source and for this
+    workload; else None.  Times a launch's algorithmic flops it gives the
+    launch's DRAM traffic (launches change with the wave budget)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -203,7 +205,7 @@ def traffic_for(kind, workload="chno1000"):
         return None
     if ent.get("workload", "chno1000") != workload:
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get("dram_bytes_per_algorithmic_flop")
 
 
 def oracle_sample(prob, D, n_batches, seed=7, keep=False):
@@ -739,7 +741,8 @@ def main():
                                       % (peak_src, products)}
                 r["frac"] = r["achieved"] / r["peak"]
                 # the committed DRAM figures were taken on the split-BF16 kernels
-                r["traffic"] = traffic_for(kind, args.workload) if args.precision == "split_bf16" else None
+                bpf = traffic_for(kind, args.workload) if args.precision == "split_bf16" else None
+                r["traffic"] = bpf * per_launch_flops if bpf is not None else None
                 # the DRAM traffic against the algorithmic bytes of the class
                 # (operand images written and read, scatter, D blocks, points)
                 alg_bytes = pk["bytes"] / max(1, pk["launches"])

@@ -124,7 +124,8 @@ int fgi_set_grid(fgi_ctx *ctx, int64_t n_pts, const double *xyz, const double *w
    (paper_2208_12335_gb300/tune.py): density_sb_points (points per density
    super-batch, 0..1024; 0 keeps the given batches), density_sb_growth (limit
    on a super-batch's active functions relative to its largest member,
-   1..16), wave_mb (operand-image workspace per wave, MiB), h_sb_points and
+   1..16), wave_mb (operand-image workspace per wave, MiB, default 8192),
+   h_sb_points and
    h_sb_growth (the same two limits for the H path; defaults 512 points and
    1.25: deeper H contractions accumulate more FP32 truncation in the
    remainder products), bound_grids (0, 1 or 2, default 2: the split images'

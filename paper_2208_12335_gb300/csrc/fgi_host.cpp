@@ -237,7 +237,12 @@ void wave_work(fgi_ctx *c);
 struct TuneSettings {
     int sb_points = 1024;
     double sb_growth = 1.35;
-    long long wave_mb = 0;      // 0: the library default
+    // operand images per wave: 8 GiB.  The persistent contraction kernels
+    // walk a wave's tile list with a fixed stride, so CTAs drift apart over
+    // a long wave and the tiles in flight outgrow L2; shorter waves re-align
+    // them (1000-atom step: density 163.8 -> 155.0 ms, step 593.1 -> 588.5 ms
+    // against 24 GiB waves) until the extra launches cost more (3 GiB: 603 ms)
+    long long wave_mb = 8192;
     // merges neighbouring batches (fewer tiles and scatter atomics); 512
     // points keep the FP32 accumulation of the remainder products (one
     // truncation per 16-point MMA step) within the H tolerance

@@ -65,10 +65,11 @@ def test_traffic_record_only_for_the_current_kernel_source(tmp_path, monkeypatch
     src.write_bytes(b"kernel source v1\n")
     import hashlib
     h = hashlib.sha256(b"kernel source v1\n").hexdigest()[:16]
-    rec = {"h": {"source": "k.cu", "source_sha256_16": h, "dram_bytes_per_launch": 123.0}}
+    rec = {"h": {"source": "k.cu", "source_sha256_16": h, "dram_bytes_per_algorithmic_flop": 0.125,
+                 "workload": "chno1000"}}
     (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.traffic_for("h") == 123.0
+    assert bench.traffic_for("h") == 0.125
     assert bench.traffic_for("density") is None
     assert bench.traffic_for("h", "si64") is None              # taken on another workload
     src.write_bytes(b"kernel source v2\n")                 # the kernel changed since the capture
