@@ -35,6 +35,12 @@ DEFAULT_CANDIDATES = [
     {"density_sb_points": 1024, "density_sb_growth": 1.2},
     {"density_sb_points": 1024, "density_sb_growth": 1.35},
     {"density_sb_points": 1024, "density_sb_growth": 1.6},
+    # operand images per wave (default 8192 MiB): the persistent contraction
+    # kernels take a wave's tiles with a fixed stride, so shorter waves keep
+    # their CTAs closer together in the tile list (less L2 thrash) at the
+    # price of more launches
+    {"wave_mb": 3072},
+    {"wave_mb": 24576},
 ]
 
 
